@@ -1,0 +1,214 @@
+/*
+ * rsgpu.h -- C ABI of the GB300 ROCKSTAR hot path.
+ *
+ * The library finds dark-matter halos in a periodic box of particles the way
+ * the ROCKSTAR halo finder does (Behroozi, Wechsler & Wu, arXiv:1110.4372):
+ *
+ *   rs_fof3d       3D friends-of-friends over the box                Sec. 3.1
+ *   rs_group_sort  groups of at least min_n particles as a CSR list  Sec. 3.1, App. A
+ *   rs_refine6d    phase-space FOF hierarchy inside every group      Sec. 3.2, Eq. 1
+ *   rs_assign      seeds, seed merge and particle assignment         Sec. 3.3, Eqs. 2-4
+ *   rs_find_halos  the four calls above in sequence, with host or device buffers
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * Pointers.    Array arguments are DEVICE pointers owned by the caller unless
+ *              stated otherwise.  Positions and velocities are float32, n rows
+ *              of `stride` floats (stride 3 or 4; x, y, z first).  Positions
+ *              lie in [0, box); velocities are in any unit.
+ * Streams.     All device work is enqueued on the context's stream.  Calls
+ *              that return host scalars synchronise that stream first.
+ * Errors.      No call aborts, traps or prints.  Every call returns an
+ *              rs_status; rs_last_error() gives a one-line message for the
+ *              last failure on that context.  Device-side failures (a bounded
+ *              wait that ran out, a table that overflowed) are recorded in a
+ *              device status word and reported by the next synchronising call.
+ * Sizes.       n < 2^31 (RS_ERR_TOO_LARGE otherwise).  n = 0 is valid.
+ * Memory.      The context owns a grow-only device workspace allocated with
+ *              cudaMalloc and freed by rs_destroy.  rs_tree objects are owned
+ *              by the library and freed by rs_tree_free.
+ * Threads.     A context may be used by one host thread at a time.
+ */
+#ifndef RSGPU_H
+#define RSGPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RS_OK = 0,
+    RS_ERR_INVALID_ARG = 1, /* a size, pointer, stride or parameter is out of range */
+    RS_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in rs_last_error) */
+    RS_ERR_OOM = 3,         /* device allocation failed */
+    RS_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out; results are invalid */
+    RS_ERR_TOO_LARGE = 5,   /* n >= 2^31, or a grid or table would exceed its index range */
+    RS_ERR_INTERNAL = 6,    /* an internal capacity or consistency check failed */
+    RS_ERR_EXTENT = 7       /* a group spans half the box or more on some axis */
+} rs_status;
+
+typedef struct rs_ctx rs_ctx;
+typedef struct rs_tree rs_tree;
+
+/* Parameters of the method (Table 2 of the paper, plus the merge threshold
+ * of Eq. 2 and the virial overdensity of Sec. 3.3). */
+typedef struct {
+    double b;            /* 3D linking length in units of the mean interparticle spacing (0.28) */
+    double f;            /* fraction of a node's particles linked at each level (0.7), 0 < f < 1 */
+    int32_t min_n;       /* smallest subgroup kept (10), >= 2 */
+    double delta_vir;    /* rho_vir / rho_background for r_dyn,vir (360) */
+    double nbar;         /* background number density; <= 0 means n / box^3 */
+    double merge_thresh; /* seeds merge below this Eq. 2 separation (10 sqrt 2) */
+} rs_params;
+
+/* Fills p with the paper's defaults: b = 0.28, f = 0.7, min_n = 10,
+ * delta_vir = 360, nbar = 0 (derived), merge_thresh = 10 sqrt 2. */
+void rs_params_default(rs_params *p);
+
+/* Creates a context bound to a CUDA stream (a cudaStream_t cast to void*;
+ * NULL = the legacy default stream) on the current device. */
+rs_status rs_create(rs_ctx **out, void *cuda_stream);
+void rs_destroy(rs_ctx *ctx);
+rs_status rs_set_stream(rs_ctx *ctx, void *cuda_stream);
+const char *rs_status_string(rs_status s);
+const char *rs_last_error(const rs_ctx *ctx);
+
+/* Sec. 3.1: the linking length b times the cube root of the mean volume per
+ * particle, l = b * cbrt(box^3 / n), in float64.  0 for n = 0. */
+double rs_linking_length(int64_t n, double box, double b);
+
+/* ------------------------------------------------------------------------ */
+/* 3D friends-of-friends (Sec. 3.1)                                          */
+/* ------------------------------------------------------------------------ */
+/* Two particles are friends when their periodic (minimum-image) distance is
+ * at most l = rs_linking_length(n, box, b); groups are the connected
+ * components.  Writes labels[i] = the smallest particle index in i's group
+ * (device, n int32).  Distances are tested in float32 and every pair within
+ * a proven float32 error band of l is re-tested in float64, so the partition
+ * equals the float64 one.
+ *   n_groups  (host, optional) number of groups, singletons included;
+ *   n_tieband (host, optional) number of pairs with |d - l| <= 1e-6 l; asking
+ *             for it runs an extra pass over every pair within 2 l.
+ * Passing either host pointer synchronises.  Errors: RS_ERR_INVALID_ARG for
+ * box <= 0, b <= 0, stride not 3 or 4, or a box narrower than about seven
+ * linking lengths; RS_ERR_TOO_LARGE for n >= 2^31 or more than 2^32 grid
+ * cells of side 4 l / sqrt 3. */
+rs_status rs_fof3d(rs_ctx *ctx, const float *pos, int32_t stride, int64_t n, double box, double b,
+                   int32_t *labels, int64_t *n_groups, int64_t *n_tieband);
+
+/* Groups with at least min_n members as a CSR list -- the work units of
+ * App. A.  perm (device, capacity n) receives the members of each such group
+ * back to back, groups ordered by label, members ascending; offsets (device,
+ * capacity offsets_cap) receives n_groups + 1 int64 boundaries.  n_groups and
+ * n_members (host) are required; the call synchronises.  RS_ERR_INTERNAL if
+ * offsets_cap < n_groups + 1 (n_groups is still written). */
+rs_status rs_group_sort(rs_ctx *ctx, const int32_t *labels, int64_t n, int32_t min_n, int32_t *perm,
+                        int64_t *offsets, int64_t offsets_cap, int64_t *n_groups, int64_t *n_members);
+
+/* ------------------------------------------------------------------------ */
+/* Phase-space hierarchy (Sec. 3.2, Eq. 1)                                   */
+/* ------------------------------------------------------------------------ */
+/* For every group g (members perm[group_offsets[g] .. group_offsets[g+1]),
+ * device) with at least min_n members: normalise positions and velocities by
+ * the node's dispersions sigma_x, sigma_v (3D totals, 1/n), find each
+ * member's nearest neighbour under Eq. 1, set the linking length to the k-th
+ * smallest nearest-neighbour distance with k = ceil(f n), take the connected
+ * components at that length, keep components of at least min_n members
+ * (and fewer than the node's) as children, and recurse.  Nodes without
+ * children are the seed halos.  Means are accumulated exactly in 64-bit
+ * fixed point, distances in float32 with a float64 recheck of every pair in
+ * the float32 error band of a linking length, so every partition equals the
+ * float64 one.  *out receives a library-owned tree (free with rs_tree_free).
+ * Synchronises.  RS_ERR_EXTENT if a node spans half the box on some axis. */
+rs_status rs_refine6d(rs_ctx *ctx, const float *pos, const float *vel, int32_t stride, int64_t n, double box,
+                      const int32_t *perm, const int64_t *group_offsets, int64_t n_groups, double f,
+                      int32_t min_n, rs_tree **out);
+
+/* Host scalars of a tree: node count, number of levels (max level + 1),
+ * seed (leaf) count, tie-band pairs over all nodes, member count (the sum of
+ * the refined groups' sizes).  Any pointer may be NULL. */
+rs_status rs_tree_info(const rs_tree *t, int64_t *n_nodes, int32_t *n_levels, int64_t *n_seeds,
+                       int64_t *n_tieband, int64_t *n_members);
+
+/* Node table, device outputs of n_nodes entries (xbar, vbar: 3 per node),
+ * each pointer optional (NULL = skip).  Members of node i are
+ * members[first[i] .. first[i] + count[i]) of rs_tree_members, its children's
+ * members at the front of that range (nested intervals).  lnk is the linking
+ * length in units of the node's own metric (Eq. 1); xbar is wrapped into
+ * [0, box); minidx is the smallest member particle index; tie counts the
+ * node's tie-band pairs (|d - l| <= 1e-6 l, d != l). */
+rs_status rs_tree_nodes(rs_ctx *ctx, const rs_tree *t, int32_t *parent, int32_t *level, int64_t *first,
+                        int64_t *count, int32_t *minidx, int32_t *nchild, double *lnk, double *xbar,
+                        double *vbar, double *sigx, double *sigv, int64_t *tie);
+
+/* Member particle indices in tree order (device, n_members int32). */
+rs_status rs_tree_members(rs_ctx *ctx, const rs_tree *t, int32_t *members);
+
+/* labels[i] (device, n int32) = the smallest member index of the node at
+ * `level` that holds particle i, or -1. */
+rs_status rs_tree_level_labels(rs_ctx *ctx, const rs_tree *t, int32_t level, int64_t n, int32_t *labels);
+
+void rs_tree_free(rs_tree *t);
+
+/* ------------------------------------------------------------------------ */
+/* Seeds, merge and assignment (Sec. 3.3, Eqs. 2-4)                           */
+/* ------------------------------------------------------------------------ */
+/* Seeds are the tree's leaves.  Within each 3D group two seeds merge when
+ * Eq. 2 with the smaller seed's Poisson uncertainties sigma/sqrt(n) is below
+ * params->merge_thresh (merges close transitively).  A halo's id is the
+ * smallest particle index among its seeds' members; its centre, bulk
+ * velocity, sigma_v and v_max come from those members, and r_dyn,vir
+ * (Eq. 4) = v_max / sqrt(4/3 pi G rho_vir) with rho_vir = delta_vir m nbar.
+ * Each particle is decided at the deepest node holding it: a seed's members
+ * go to its halo; a node's other members go to its only halo if its seeds
+ * form one, else to the halo nearest under Eq. 3 (ties to the smaller id).
+ * halo_id (device, n int32) gets the halo id or -1 outside refined groups;
+ * n_halos (host, optional) synchronises.  The same pos/vel as rs_refine6d. */
+rs_status rs_assign(rs_ctx *ctx, const rs_tree *t, const float *pos, const float *vel, int32_t stride, int64_t n,
+                    double box, const rs_params *params, int32_t *halo_id, int64_t *n_halos);
+
+/* ------------------------------------------------------------------------ */
+/* Whole path                                                                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n_fof_groups;   /* 3D groups with >= min_n members */
+    int64_t n_members;      /* particles in those groups */
+    int64_t n_nodes;        /* hierarchy nodes */
+    int32_t n_levels;
+    int64_t n_seeds;
+    int64_t n_halos;
+    int64_t n_tieband6d;
+    int64_t sum_level_members; /* members summed over all nodes (for byte counts) */
+} rs_stats;
+
+/* rs_fof3d + rs_group_sort + rs_refine6d + rs_assign.  With host_buffers =
+ * 0, pos, vel, fof_labels and halo_id are device pointers; with
+ * host_buffers = 1 they are host pointers (pinned memory gives full copy
+ * speed): the inputs are copied to the context's workspace and both outputs
+ * copied back before the call returns.  fof_labels and stats may be NULL.
+ * Synchronises. */
+rs_status rs_find_halos(rs_ctx *ctx, const float *pos, const float *vel, int32_t stride, int64_t n, double box,
+                        const rs_params *params, int32_t *fof_labels, int32_t *halo_id, rs_stats *stats,
+                        int32_t host_buffers);
+
+/* ------------------------------------------------------------------------ */
+/* Instrumentation                                                           */
+/* ------------------------------------------------------------------------ */
+/* When enabled, every kernel launch on the context is bracketed by CUDA
+ * events on the context's stream; rs_profile_read (synchronises) returns per
+ * kernel name the launch count and total device milliseconds. */
+rs_status rs_profile_enable(rs_ctx *ctx, int32_t on);
+void rs_profile_reset(rs_ctx *ctx);
+int32_t rs_profile_count(rs_ctx *ctx);
+rs_status rs_profile_read(rs_ctx *ctx, int32_t i, const char **name, int64_t *launches, double *total_ms);
+/* Number of kernel launches issued on the context since the last reset
+ * (counted whether or not profiling is enabled). */
+int64_t rs_launch_count(const rs_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSGPU_H */

@@ -1,0 +1,528 @@
+// rs_fof3d.cu -- periodic 3D friends-of-friends (Sec. 3.1) and the group CSR.
+//
+// Particles are binned into fine cells of side s <= l / sqrt(3) (with a
+// margin that covers the float32 rounding of the cell index), so any two
+// particles of one fine cell are friends and a fine cell can stand for all
+// of its particles in the union-find.  Fine cells are grouped 4 x 4 x 4 into
+// coarse cells; particles are radix-sorted by (coarse cell, fine sub-cell)
+// and a dense table maps each coarse cell to its first fine cell.  Every
+// friend of a particle lies within two fine cells per axis, which is inside
+// at most 2 x 2 x 2 coarse cells.  Two fine cells are joined as soon as one
+// pair between them is within l; pairs already in one set are skipped.
+//
+// Distances: float32 with the periodic shift applied to the coordinate near
+// the top of the box (x - box is exact there), compared against l^2 (1 -+
+// 2^-20); pairs inside that band are re-tested in float64 with the same
+// separate multiplies and adds as the definition, so the partition is the
+// float64 one.
+#include <cmath>
+
+#include "rs_internal.cuh"
+
+namespace {
+
+constexpr int FOF_THREADS = 256;
+constexpr double BAND_REL = 9.5367431640625e-07;  // 2^-20, relative on d^2
+
+struct FofGeom {
+    int32_t Gc;      // coarse cells per side
+    int32_t Gf;      // fine cells per side (4 Gc)
+    float inv_sf;    // Gf / box (float32)
+    float boxf;
+    double box;
+    double l, l2;
+    float lo32, hi32;  // float32 thresholds on d^2 around l^2
+};
+
+__device__ __forceinline__ void load_pos(const float *pos, int stride, int64_t i, float &x, float &y, float &z)
+{
+    const float *p = pos + (int64_t)stride * i;
+    x = p[0];
+    y = p[1];
+    z = p[2];
+}
+
+__device__ __forceinline__ int fine_coord(float x, float inv, int Gf)
+{
+    int f = (int)floorf(x * inv);
+    f = f < 0 ? 0 : f;
+    f = f >= Gf ? Gf - 1 : f;
+    return f;
+}
+
+__global__ void k_fof_keys(const float *pos, int stride, int64_t n, FofGeom g, uint64_t *keys, uint32_t *vals,
+                           rs_dev_status *st)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float x, y, z;
+    load_pos(pos, stride, i, x, y, z);
+    if (!(x >= 0.f && x < g.boxf && y >= 0.f && y < g.boxf && z >= 0.f && z < g.boxf))
+        dev_fail(st, DEV_BADARG, 10, i);
+    int fx = fine_coord(x, g.inv_sf, g.Gf), fy = fine_coord(y, g.inv_sf, g.Gf), fz = fine_coord(z, g.inv_sf, g.Gf);
+    uint64_t c = ((uint64_t)(fz >> 2) * (uint64_t)g.Gc + (uint64_t)(fy >> 2)) * (uint64_t)g.Gc + (uint64_t)(fx >> 2);
+    uint32_t sub = (uint32_t)(((fz & 3) << 4) | ((fy & 3) << 2) | (fx & 3));
+    keys[i] = (c << 6) | sub;
+    vals[i] = (uint32_t)i;
+}
+
+// sorted positions as float4 and cell-start flags
+__global__ void k_fof_gather(const float *pos, int stride, int64_t n, const uint64_t *keys, const uint32_t *idx,
+                             float4 *spos, uint32_t *flag)
+{
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    float x, y, z;
+    load_pos(pos, stride, idx[q], x, y, z);
+    spos[q] = make_float4(x, y, z, 0.f);
+    flag[q] = (q == 0 || keys[q] != keys[q - 1]) ? 1u : 0u;
+}
+
+// after an exclusive scan of flag: cell_of[q] = scan[q] + flag[q] - 1
+__global__ void k_fof_cells(int64_t n, const uint64_t *keys, const uint32_t *scan, const uint32_t *flag,
+                            uint32_t *cell_of, uint32_t *cell_start, uint64_t *cell_key, uint32_t *table,
+                            const uint32_t *n_cells)
+{
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    uint32_t c = scan[q] + flag[q] - 1u;
+    cell_of[q] = c;
+    if (flag[q]) {
+        cell_start[c] = (uint32_t)q;
+        cell_key[c] = keys[q];
+        uint64_t coarse = keys[q] >> 6;
+        if (q == 0 || (keys[q - 1] >> 6) != coarse) table[coarse] = c;
+    }
+    if (q == n - 1) cell_start[*n_cells] = (uint32_t)n;
+}
+
+__global__ void k_fill_u32(uint32_t *p, int64_t n, uint32_t v)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < n; i += stride) p[i] = v;
+}
+
+__global__ void k_iota_i32(int *p, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = (int)i;
+}
+
+__device__ __forceinline__ void cell_coords(uint64_t key, int Gc, int &fx, int &fy, int &fz)
+{
+    uint64_t c = key >> 6;
+    int sub = (int)(key & 63);
+    int cx = (int)(c % (uint64_t)Gc);
+    uint64_t r = c / (uint64_t)Gc;
+    int cy = (int)(r % (uint64_t)Gc);
+    int cz = (int)(r / (uint64_t)Gc);
+    fx = 4 * cx + (sub & 3);
+    fy = 4 * cy + ((sub >> 2) & 3);
+    fz = 4 * cz + ((sub >> 4) & 3);
+}
+
+// wrapped fine-cell offset b - a in [-Gf/2, Gf/2); shift tells which point
+// sits on the far side of the periodic face (+1: b near the top, -1: a)
+__device__ __forceinline__ int fine_offset(int a, int b, int Gf, int &shift)
+{
+    int d = b - a;
+    shift = 0;
+    if (d > Gf / 2) {
+        d -= Gf;
+        shift = 1;
+    } else if (d < -(Gf / 2)) {
+        d += Gf;
+        shift = -1;
+    }
+    return d;
+}
+
+__device__ __forceinline__ float sdiff(float a, float b, int shift, float box)
+{
+    // b - a with the periodic image chosen by shift; x - box is exact for x >= box/2
+    if (shift > 0) return (b - box) - a;
+    if (shift < 0) return b - (a - box);
+    return b - a;
+}
+
+__device__ __forceinline__ double ddiff(float a, float b, int shift, double box)
+{
+    if (shift > 0) return f64_sub(f64_sub((double)b, box), (double)a);
+    if (shift < 0) return f64_sub((double)b, f64_sub((double)a, box));
+    return f64_sub((double)b, (double)a);
+}
+
+// 0 = not friends, 1 = friends
+__device__ __forceinline__ int pair_link(const float4 &pa, const float4 &pb, int sx, int sy, int sz,
+                                         const FofGeom &g)
+{
+    float dx = sdiff(pa.x, pb.x, sx, g.boxf), dy = sdiff(pa.y, pb.y, sy, g.boxf), dz = sdiff(pa.z, pb.z, sz, g.boxf);
+    float d2 = dx * dx + dy * dy + dz * dz;
+    if (d2 <= g.lo32) return 1;
+    if (d2 > g.hi32) return 0;
+    double ex = ddiff(pa.x, pb.x, sx, g.box), ey = ddiff(pa.y, pb.y, sy, g.box), ez = ddiff(pa.z, pb.z, sz, g.box);
+    double e2 = f64_add(f64_add(f64_mul(ex, ex), f64_mul(ey, ey)), f64_mul(ez, ez));
+    return e2 <= g.l2 ? 1 : 0;
+}
+
+// One thread per fine cell: join it with every fine cell of larger index
+// within two fine cells per axis that has a friend pair with it.
+__global__ void __launch_bounds__(FOF_THREADS) k_fof_link(int64_t n_cells_cap, const uint32_t *n_cells_p,
+                                                            const uint64_t *cell_key, const uint32_t *cell_start,
+                                                            const uint32_t *table, const float4 *spos, int *parent,
+                                                            FofGeom g, rs_dev_status *st)
+{
+    const int64_t M = *n_cells_p;
+    for (int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; A < M; A += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t ka = cell_key[A];
+        int ax, ay, az;
+        cell_coords(ka, g.Gc, ax, ay, az);
+        const uint32_t a0 = cell_start[A], a1 = cell_start[A + 1];
+        const int ccx = ax >> 2, ccy = ay >> 2, ccz = az >> 2;
+        const int lox = (ax & 3) < 2 ? -1 : 0, loy = (ay & 3) < 2 ? -1 : 0, loz = (az & 3) < 2 ? -1 : 0;
+        for (int dz = loz; dz <= loz + 1; dz++) {
+            int cz = ccz + dz;
+            cz = cz < 0 ? cz + g.Gc : (cz >= g.Gc ? cz - g.Gc : cz);
+            for (int dy = loy; dy <= loy + 1; dy++) {
+                int cy = ccy + dy;
+                cy = cy < 0 ? cy + g.Gc : (cy >= g.Gc ? cy - g.Gc : cy);
+                for (int dx = lox; dx <= lox + 1; dx++) {
+                    int cx = ccx + dx;
+                    cx = cx < 0 ? cx + g.Gc : (cx >= g.Gc ? cx - g.Gc : cx);
+                    const uint64_t cc = ((uint64_t)cz * g.Gc + cy) * g.Gc + cx;
+                    const uint32_t b0c = table[cc];
+                    if (b0c == 0xffffffffu) continue;
+                    for (int64_t B = b0c; B < M && (cell_key[B] >> 6) == cc; B++) {
+                        if (B <= A) continue;
+                        int bx, by, bz;
+                        cell_coords(cell_key[B], g.Gc, bx, by, bz);
+                        int sx, sy, sz;
+                        int ox = fine_offset(ax, bx, g.Gf, sx), oy = fine_offset(ay, by, g.Gf, sy),
+                            oz = fine_offset(az, bz, g.Gf, sz);
+                        if (ox < -2 || ox > 2 || oy < -2 || oy > 2 || oz < -2 || oz > 2) continue;
+                        if (uf_find(parent, (int)A, st) == uf_find(parent, (int)B, st)) continue;
+                        const uint32_t b0 = cell_start[B], b1 = cell_start[B + 1];
+                        bool linked = false;
+                        for (uint32_t i = a0; i < a1 && !linked; i++) {
+                            const float4 pa = spos[i];
+                            for (uint32_t j = b0; j < b1; j++)
+                                if (pair_link(pa, spos[j], sx, sy, sz, g)) {
+                                    linked = true;
+                                    break;
+                                }
+                        }
+                        if (linked) uf_union(parent, (int)A, (int)B, st);
+                    }
+                }
+            }
+        }
+    }
+}
+
+__global__ void k_fof_rootmin(const uint32_t *n_cells_p, const uint32_t *cell_start, const uint32_t *idx,
+                              int *parent, int *root_min, rs_dev_status *st)
+{
+    const int64_t M = *n_cells_p;
+    for (int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; A < M; A += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t m = 0xffffffffu;
+        for (uint32_t q = cell_start[A]; q < cell_start[A + 1]; q++) m = min(m, idx[q]);
+        int r = uf_find(parent, (int)A, st);
+        atomicMin(&root_min[r], (int)m);
+    }
+}
+
+__global__ void k_fof_labels(int64_t n, const uint32_t *idx, const uint32_t *cell_of, int *parent,
+                             const int *root_min, int32_t *labels, rs_dev_status *st)
+{
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    labels[idx[q]] = root_min[uf_find(parent, (int)cell_of[q], st)];
+}
+
+__global__ void k_fof_count_roots(const uint32_t *n_cells_p, const int *parent, unsigned long long *count)
+{
+    const int64_t M = *n_cells_p;
+    unsigned long long c = 0;
+    for (int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; A < M; A += (int64_t)gridDim.x * blockDim.x)
+        c += parent[A] == (int)A ? 1ull : 0ull;
+    c = warp_sum(c);
+    if (lane_id() == 0 && c) atomicAdd(count, c);
+}
+
+// Tie-band census: every pair (i < j in sorted order) within the fine-cell
+// reach whose float64 distance satisfies |d - l| <= 1e-6 l.
+__global__ void __launch_bounds__(FOF_THREADS) k_fof_tieband(const uint32_t *n_cells_p, const uint64_t *cell_key,
+                                                               const uint32_t *cell_start, const uint32_t *table,
+                                                               const float4 *spos, FofGeom g,
+                                                               unsigned long long *count)
+{
+    const int64_t M = *n_cells_p;
+    const float flo = (float)(g.l2 * (1.0 - 4e-6)), fhi = (float)(g.l2 * (1.0 + 4e-6));
+    unsigned long long c = 0;
+    for (int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; A < M; A += (int64_t)gridDim.x * blockDim.x) {
+        int ax, ay, az;
+        cell_coords(cell_key[A], g.Gc, ax, ay, az);
+        const uint32_t a0 = cell_start[A], a1 = cell_start[A + 1];
+        const int lox = (ax & 3) < 2 ? -1 : 0, loy = (ay & 3) < 2 ? -1 : 0, loz = (az & 3) < 2 ? -1 : 0;
+        for (int dz = loz; dz <= loz + 1; dz++)
+            for (int dy = loy; dy <= loy + 1; dy++)
+                for (int dx = lox; dx <= lox + 1; dx++) {
+                    int cx = (ax >> 2) + dx, cy = (ay >> 2) + dy, cz = (az >> 2) + dz;
+                    cx = cx < 0 ? cx + g.Gc : (cx >= g.Gc ? cx - g.Gc : cx);
+                    cy = cy < 0 ? cy + g.Gc : (cy >= g.Gc ? cy - g.Gc : cy);
+                    cz = cz < 0 ? cz + g.Gc : (cz >= g.Gc ? cz - g.Gc : cz);
+                    const uint64_t cc = ((uint64_t)cz * g.Gc + cy) * g.Gc + cx;
+                    const uint32_t b0c = table[cc];
+                    if (b0c == 0xffffffffu) continue;
+                    for (int64_t B = b0c; B < M && (cell_key[B] >> 6) == cc; B++) {
+                        if (B < A) continue;
+                        int bx, by, bz, sx, sy, sz;
+                        cell_coords(cell_key[B], g.Gc, bx, by, bz);
+                        int ox = fine_offset(ax, bx, g.Gf, sx), oy = fine_offset(ay, by, g.Gf, sy),
+                            oz = fine_offset(az, bz, g.Gf, sz);
+                        if (ox < -2 || ox > 2 || oy < -2 || oy > 2 || oz < -2 || oz > 2) continue;
+                        for (uint32_t i = a0; i < a1; i++) {
+                            const float4 pa = spos[i];
+                            for (uint32_t j = (B == A ? i + 1 : cell_start[B]); j < cell_start[B + 1]; j++) {
+                                const float4 pb = spos[j];
+                                float ddx = sdiff(pa.x, pb.x, sx, g.boxf), ddy = sdiff(pa.y, pb.y, sy, g.boxf),
+                                      ddz = sdiff(pa.z, pb.z, sz, g.boxf);
+                                float d2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                                if (d2 < flo || d2 > fhi) continue;
+                                double ex = ddiff(pa.x, pb.x, sx, g.box), ey = ddiff(pa.y, pb.y, sy, g.box),
+                                       ez = ddiff(pa.z, pb.z, sz, g.box);
+                                double d = sqrt(f64_add(f64_add(f64_mul(ex, ex), f64_mul(ey, ey)), f64_mul(ez, ez)));
+                                if (fabs(d - g.l) <= 1e-6 * g.l) c++;
+                            }
+                        }
+                    }
+                }
+    }
+    c = warp_sum(c);
+    if (lane_id() == 0 && c) atomicAdd(count, c);
+}
+
+rs_status fof_geometry(rs_ctx *ctx, int64_t n, double box, double b, FofGeom *g)
+{
+    double l = rs_linking_length(n, box, b);
+    if (!(l > 0)) return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_fof3d: linking length must be positive");
+    // fine side s with sqrt(3) s (1 + 2 err) < l, err = float32 error of the
+    // fine-cell coordinate in cell units (2.0001 u Gf)
+    const double u = 5.9604644775390625e-08;
+    double gf_est = box * std::sqrt(3.0) / l + 16.0;
+    double err = 2.0001 * u * gf_est * 1.01;
+    double s_max = l * (1.0 - 1e-7) / (std::sqrt(3.0) * (1.0 + 2.0 * err));
+    double gc = std::ceil(box / (4.0 * s_max));
+    if (gc < 3) return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_fof3d: box narrower than about seven linking lengths");
+    if (gc * gc * gc >= 4294967295.0) return rs_fail(ctx, RS_ERR_TOO_LARGE, "rs_fof3d: more than 2^32 coarse cells");
+    g->Gc = (int32_t)gc;
+    g->Gf = 4 * g->Gc;
+    if (g->Gf > gf_est) return rs_fail(ctx, RS_ERR_INTERNAL, "rs_fof3d: grid estimate");
+    g->inv_sf = (float)((double)g->Gf / box);
+    g->boxf = (float)box;
+    g->box = box;
+    g->l = l;
+    g->l2 = l * l;
+    g->lo32 = (float)(g->l2 * (1.0 - BAND_REL));
+    g->hi32 = (float)(g->l2 * (1.0 + BAND_REL));
+    if ((double)g->boxf != box) return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_fof3d: box must be a float32 value");
+    return RS_OK;
+}
+
+int key_bits(const FofGeom &g)
+{
+    uint64_t maxkey = (((uint64_t)g.Gc * g.Gc * g.Gc) << 6);
+    int bits = 0;
+    while (bits < 64 && (maxkey >> bits) != 0) bits++;
+    return bits;
+}
+
+}  // namespace
+
+extern "C" rs_status rs_fof3d(rs_ctx *ctx, const float *pos, int32_t stride, int64_t n, double box, double b,
+                              int32_t *labels, int64_t *n_groups, int64_t *n_tieband)
+{
+    if (!ctx) return RS_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!pos || !labels)) || (stride != 3 && stride != 4) || !(box > 0) || !(b > 0))
+        return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_fof3d: bad argument");
+    if (n >= ((int64_t)1 << 31)) return rs_fail(ctx, RS_ERR_TOO_LARGE, "rs_fof3d: n >= 2^31");
+    if (n == 0) {
+        if (n_groups) *n_groups = 0;
+        if (n_tieband) *n_tieband = 0;
+        return RS_OK;
+    }
+    FofGeom g;
+    RS_TRY(fof_geometry(ctx, n, box, b, &g));
+    const int64_t T = FOF_THREADS;
+    const int64_t nb = ceil_div(n, T);
+    const int64_t ncoarse = (int64_t)g.Gc * g.Gc * g.Gc;
+
+    RS_WS(ctx, uint64_t, k0, WS_SORT_K0, n);
+    RS_WS(ctx, uint64_t, k1, WS_SORT_K1, n);
+    RS_WS(ctx, uint32_t, v0, WS_SORT_V0, n);
+    RS_WS(ctx, uint32_t, v1, WS_SORT_V1, n);
+    RS_LAUNCH(ctx, "fof_keys", k_fof_keys, nb, T, 0, pos, stride, n, g, k0, v0, ctx->d_status);
+    bool alt = false;
+    RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, n, key_bits(g), &alt));
+    uint64_t *keys = alt ? k1 : k0;
+    uint32_t *idx = alt ? v1 : v0;
+
+    RS_WS(ctx, float4, spos, WS_FOF_POS4, n);
+    RS_WS(ctx, uint32_t, flag, WS_FOF_MISC, 2 * n + 8);
+    uint32_t *scan = flag + n;
+    uint32_t *n_cells = flag + 2 * n;  // device scalar
+    RS_LAUNCH(ctx, "fof_gather", k_fof_gather, nb, T, 0, pos, stride, n, (const uint64_t *)keys,
+              (const uint32_t *)idx, spos, flag);
+    RS_CUDA(ctx, cudaMemcpyAsync(scan, flag, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    RS_TRY(rs_scan_u32(ctx, scan, n, n_cells));
+
+    RS_WS(ctx, uint32_t, cell_of, WS_FOF_CELLOF, n);
+    RS_WS(ctx, uint32_t, cell_start, WS_FOF_CELLSTART, n + 1);
+    RS_WS(ctx, uint64_t, cell_key, WS_FOF_CELLKEY, n);
+    RS_WS(ctx, uint32_t, table, WS_FOF_TABLE, ncoarse);
+    int fill_blocks = (int)std::min<int64_t>(ceil_div(ncoarse, T), (int64_t)ctx->num_sms * 16);
+    RS_LAUNCH(ctx, "fof_table_clear", k_fill_u32, fill_blocks, T, 0, table, ncoarse, 0xffffffffu);
+    RS_LAUNCH(ctx, "fof_cells", k_fof_cells, nb, T, 0, n, (const uint64_t *)keys, (const uint32_t *)scan,
+              (const uint32_t *)flag, cell_of, cell_start, cell_key, table, (const uint32_t *)n_cells);
+
+    RS_WS(ctx, int, parent, WS_FOF_PARENT, n);
+    RS_WS(ctx, int, root_min, WS_FOF_ROOTMIN, n);
+    RS_LAUNCH(ctx, "fof_iota", k_iota_i32, nb, T, 0, parent, n);
+    RS_LAUNCH(ctx, "fof_fill", k_fill_u32, std::min<int64_t>(nb, (int64_t)ctx->num_sms * 16), T, 0,
+              (uint32_t *)root_min, n, 0x7fffffffu);
+    const int64_t grid = std::min<int64_t>(nb, (int64_t)ctx->num_sms * 32);
+    RS_LAUNCH(ctx, "fof_link", k_fof_link, grid, T, 0, n, (const uint32_t *)n_cells, (const uint64_t *)cell_key,
+              (const uint32_t *)cell_start, (const uint32_t *)table, (const float4 *)spos, parent, g,
+              ctx->d_status);
+    RS_LAUNCH(ctx, "fof_rootmin", k_fof_rootmin, grid, T, 0, (const uint32_t *)n_cells,
+              (const uint32_t *)cell_start, (const uint32_t *)idx, parent, root_min, ctx->d_status);
+    RS_LAUNCH(ctx, "fof_labels", k_fof_labels, nb, T, 0, n, (const uint32_t *)idx, (const uint32_t *)cell_of,
+              parent, (const int *)root_min, labels, ctx->d_status);
+    if (n_groups || n_tieband) {
+        unsigned long long *cnt = (unsigned long long *)(flag + 2 * n + 2);
+        RS_CUDA(ctx, cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), ctx->stream));
+        if (n_groups)
+            RS_LAUNCH(ctx, "fof_count_roots", k_fof_count_roots, grid, T, 0, (const uint32_t *)n_cells,
+                      (const int *)parent, cnt);
+        if (n_tieband)
+            RS_LAUNCH(ctx, "fof_tieband", k_fof_tieband, grid, T, 0, (const uint32_t *)n_cells,
+                      (const uint64_t *)cell_key, (const uint32_t *)cell_start, (const uint32_t *)table,
+                      (const float4 *)spos, g, cnt + 1);
+        int64_t h[2];
+        RS_TRY(rs_read_i64(ctx, cnt, 2, h, "rs_fof3d"));
+        if (n_groups) *n_groups = h[0];
+        if (n_tieband) *n_tieband = h[1];
+    }
+    return RS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// group CSR (App. A work units)
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_gs_count(int64_t n, const int32_t *labels, uint32_t *count, rs_dev_status *st)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t l = labels[i];
+    if (l < 0 || l > i) {
+        dev_fail(st, DEV_BADARG, 20, i);
+        return;
+    }
+    atomicAdd(&count[l], 1u);
+}
+
+// root flags: groups of >= min_n members, keyed by their label (= root index)
+__global__ void k_gs_rootflag(int64_t n, const int32_t *labels, const uint32_t *count, int32_t min_n,
+                              uint32_t *rflag)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    rflag[i] = (labels[i] == (int32_t)i && count[i] >= (uint32_t)min_n) ? 1u : 0u;  // label i is in range
+}
+
+// member flags
+__global__ void k_gs_memflag(int64_t n, const int32_t *labels, const uint32_t *count, int32_t min_n,
+                             uint32_t *mflag)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t l = labels[i];
+    mflag[i] = (l >= 0 && l <= i && count[l] >= (uint32_t)min_n) ? 1u : 0u;
+}
+
+__global__ void k_gs_compact(int64_t n, const int32_t *labels, const uint32_t *mflag, const uint32_t *mscan,
+                             const uint32_t *rscan, uint32_t *keys, uint32_t *vals)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !mflag[i]) return;
+    uint32_t p = mscan[i];
+    keys[p] = rscan[labels[i]];
+    vals[p] = (uint32_t)i;
+}
+
+__global__ void k_gs_sizes(int64_t n, const uint32_t *rflag, const uint32_t *rscan, const uint32_t *count,
+                           int64_t *offsets)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !rflag[i]) return;
+    offsets[rscan[i]] = count[i];
+}
+
+}  // namespace
+
+extern "C" rs_status rs_group_sort(rs_ctx *ctx, const int32_t *labels, int64_t n, int32_t min_n, int32_t *perm,
+                                   int64_t *offsets, int64_t offsets_cap, int64_t *n_groups, int64_t *n_members)
+{
+    if (!ctx) return RS_ERR_INVALID_ARG;
+    if (n < 0 || !n_groups || !n_members || min_n < 1 || offsets_cap < 1 || !offsets ||
+        (n > 0 && (!labels || !perm)))
+        return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_group_sort: bad argument");
+    if (n >= ((int64_t)1 << 31)) return rs_fail(ctx, RS_ERR_TOO_LARGE, "rs_group_sort: n >= 2^31");
+    if (n == 0) {
+        *n_groups = 0;
+        *n_members = 0;
+        RS_CUDA(ctx, cudaMemsetAsync(offsets, 0, sizeof(int64_t), ctx->stream));
+        return RS_OK;
+    }
+    const int64_t T = 256, nb = ceil_div(n, T);
+    RS_WS(ctx, uint32_t, count, WS_GS_COUNT, n);
+    RS_WS(ctx, uint32_t, fl, WS_GS_FLAG, 4 * n + 8);
+    uint32_t *rflag = fl, *rscan = fl + n, *mflag = fl + 2 * n, *mscan = fl + 3 * n;
+    uint32_t *tot = fl + 4 * n;  // [0] groups, [1] members
+    RS_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(uint32_t) * n, ctx->stream));
+    RS_LAUNCH(ctx, "gs_count", k_gs_count, nb, T, 0, n, labels, count, ctx->d_status);
+    RS_LAUNCH(ctx, "gs_rootflag", k_gs_rootflag, nb, T, 0, n, labels, (const uint32_t *)count, min_n, rflag);
+    RS_LAUNCH(ctx, "gs_memflag", k_gs_memflag, nb, T, 0, n, labels, (const uint32_t *)count, min_n, mflag);
+    RS_CUDA(ctx, cudaMemcpyAsync(rscan, rflag, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    RS_CUDA(ctx, cudaMemcpyAsync(mscan, mflag, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    RS_TRY(rs_scan_u32(ctx, rscan, n, tot));
+    RS_TRY(rs_scan_u32(ctx, mscan, n, tot + 1));
+    uint32_t h2[2];
+    RS_CUDA(ctx, cudaMemcpyAsync(ctx->h_scratch, tot, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    RS_TRY(rs_sync_check(ctx, "rs_group_sort"));
+    memcpy(h2, ctx->h_scratch, sizeof h2);
+    const int64_t G = h2[0], Mm = h2[1];
+    *n_groups = G;
+    *n_members = Mm;
+    if (offsets_cap < G + 1) return rs_fail(ctx, RS_ERR_INTERNAL, "rs_group_sort: offsets capacity too small");
+    RS_WS(ctx, uint64_t, kbuf, WS_SORT_K0, 2 * Mm);  // reused as two u32 key arrays
+    uint32_t *k0 = (uint32_t *)kbuf, *k1 = (uint32_t *)kbuf + Mm;
+    RS_WS(ctx, uint32_t, vtmp, WS_SORT_V1, Mm);
+    uint32_t *v0 = (uint32_t *)perm;
+    RS_LAUNCH(ctx, "gs_compact", k_gs_compact, nb, T, 0, n, labels, (const uint32_t *)mflag,
+              (const uint32_t *)mscan, (const uint32_t *)rscan, k0, v0);
+    int bits = 0;
+    while (bits < 32 && ((uint64_t)(G > 0 ? G - 1 : 0) >> bits) != 0) bits++;
+    bool alt = false;
+    RS_TRY(rs_radix_sort_u32(ctx, k0, k1, v0, vtmp, Mm, bits, &alt));
+    if (alt)
+        RS_CUDA(ctx, cudaMemcpyAsync(perm, vtmp, sizeof(uint32_t) * Mm, cudaMemcpyDeviceToDevice, ctx->stream));
+    RS_CUDA(ctx, cudaMemsetAsync(offsets, 0, sizeof(int64_t) * (G + 1), ctx->stream));
+    RS_LAUNCH(ctx, "gs_sizes", k_gs_sizes, nb, T, 0, n, (const uint32_t *)rflag, (const uint32_t *)rscan,
+              (const uint32_t *)count, offsets);
+    RS_TRY(rs_scan_i64(ctx, offsets, G + 1, nullptr));
+    return rs_sync_check(ctx, "rs_group_sort");
+}

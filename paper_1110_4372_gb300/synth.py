@@ -171,7 +171,7 @@ def generate(name: str = "c1", *, seed: int | None = None, n: int | None = None,
         seed = BASE_SEED + CONFIG_INDEX[name]
     rng = np.random.Generator(np.random.PCG64(seed))
     N = cfg["n"]
-    L = cfg["box"]
+    L = float(np.float32(cfg["box"]))  # the box side is a float32 value
     nbar = N / L ** 3
     comp_n, comp_parent, comp_center, comp_bulk, comp_mass = _components(rng, cfg, nbar)
     n_halo_particles = int(comp_n.sum())
@@ -228,6 +228,7 @@ def generate(name: str = "c1", *, seed: int | None = None, n: int | None = None,
 def uniform(n: int, box: float, seed: int, vel_sigma: float = 20.0) -> Catalogue:
     """Plain uniform box (no halos), for edge cases and small tests."""
     rng = np.random.Generator(np.random.PCG64(seed))
+    box = float(np.float32(box))
     pos = _wrap32(rng.random((n, 3)) * box, box)
     vel = (rng.standard_normal((n, 3)) * vel_sigma).astype(np.float32)
     return Catalogue(pos=pos, vel=vel, box=box, truth=np.full(n, -1, np.int32),

@@ -1,0 +1,251 @@
+"""Parity of the CUDA path (through the C ABI) with the float64 oracle.
+
+Bar: 3D labels, group CSR, node member sets and halo ids equal the oracle's
+exactly (a node difference is excused only below a node with tie-band pairs,
+and counted); sigma_x, sigma_v and linking lengths within 1e-6 relative;
+centres within 1e-6 sigma."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1110_4372_gb300 import synth
+
+from gpu_util import compare_trees, cuda_inputs, gpu_tree_dict, oracle_tree_dict, run_gpu_path, run_oracle_path
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rs():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1110_4372_gb300 import rsgpu
+    return rsgpu
+
+
+@pytest.fixture(scope="module")
+def ctx(rs):
+    return rs.Context()
+
+
+def _small(seed, n=4000, halos=10, nmax=4000, sub=0):
+    box = 10.0 * (n / 32768) ** (1 / 3)
+    return synth.generate("c1", seed=seed, n=n, box=box, n_halos=halos)
+
+
+# ---------------------------------------------------------------------------
+# 3D friends-of-friends
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("stride", [3, 4])
+def test_fof3d_c1_exact(rs, ctx, stride):
+    c = synth.generate("c1")
+    pos, _ = cuda_inputs(c, stride)
+    lab, ng, nt = rs.rs_fof3d(ctx, pos, c.box, 0.28, want_groups=True, want_tieband=True)
+    ref, l, _ = oracle.fof3d(c.pos, c.box, 0.28)
+    assert np.array_equal(lab.cpu().numpy(), ref)
+    assert ng == len(np.unique(ref))
+    assert nt == oracle.fof3d_tieband(c.pos, c.box, l)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_fof3d_uniform_dense(rs, ctx, seed):
+    c = synth.uniform(6000, 10.0, seed)
+    pos, _ = cuda_inputs(c)
+    for b in (0.2, 0.6, 0.9):
+        lab, _, _ = rs.rs_fof3d(ctx, pos, c.box, b)
+        ref, _, _ = oracle.fof3d(c.pos, c.box, b)
+        assert np.array_equal(lab.cpu().numpy(), ref), b
+
+
+def test_fof3d_periodic_faces(rs, ctx):
+    rng = np.random.default_rng(5)
+    box = 10.0
+    n = 3000
+    # particles crowded against every face, edge and corner
+    p = rng.random((n, 3)) * 0.3
+    flip = rng.random((n, 3)) < 0.5
+    p = np.where(flip, box - p, p)
+    c = synth.Catalogue(pos=synth.wrap(p, box), vel=np.zeros((n, 3), np.float32), box=box,
+                        truth=np.zeros(n, np.int32), comp_parent=np.zeros(0, np.int32), comp_n=np.zeros(0))
+    pos, _ = cuda_inputs(c)
+    for b in (0.1, 0.3):
+        lab, _, _ = rs.rs_fof3d(ctx, pos, box, b)
+        ref, _, _ = oracle.fof3d(c.pos, box, b)
+        assert np.array_equal(lab.cpu().numpy(), ref), b
+
+
+def test_fof3d_lattice_closed_form(rs, ctx):
+    m = 16
+    g = (np.arange(m) + 0.5).astype(np.float32)
+    pos = np.array(np.meshgrid(g, g, g, indexing="ij"), np.float32).reshape(3, -1).T.copy()
+    box = float(m)
+    # l = b * spacing; spacing = 1 here
+    t = torch.from_numpy(pos).cuda()
+    lab, _, _ = rs.rs_fof3d(ctx, t, box, 1.0 + 1e-3)
+    assert np.all(lab.cpu().numpy() == 0)
+    lab, _, _ = rs.rs_fof3d(ctx, t, box, 1.0 - 1e-3)
+    assert np.array_equal(lab.cpu().numpy(), np.arange(len(pos)))
+
+
+def test_fof3d_empty_and_tiny(rs, ctx):
+    lab, ng, _ = rs.rs_fof3d(ctx, torch.zeros((0, 3), device="cuda"), 10.0, 0.28, want_groups=True)
+    assert lab.numel() == 0 and ng == 0
+
+
+def test_fof3d_bad_args(rs, ctx):
+    pos = torch.rand((100, 3), device="cuda") * 10
+    with pytest.raises(rs.RsError):
+        rs.rs_fof3d(ctx, pos, -1.0, 0.28)
+    with pytest.raises(rs.RsError):
+        rs.rs_fof3d(ctx, pos, 10.0, 0.0)
+
+
+# ---------------------------------------------------------------------------
+# group CSR
+# ---------------------------------------------------------------------------
+def test_group_sort_c1(rs, ctx):
+    c = synth.generate("c1")
+    pos, _ = cuda_inputs(c)
+    lab, _, _ = rs.rs_fof3d(ctx, pos, c.box, 0.28)
+    perm, off = rs.rs_group_sort(ctx, lab, 10)
+    ref_lab, _, _ = oracle.fof3d(c.pos, c.box, 0.28)
+    m, o = oracle.groups_from_labels(ref_lab, 10)
+    assert np.array_equal(perm.cpu().numpy(), m)
+    assert np.array_equal(off.cpu().numpy(), o)
+
+
+# ---------------------------------------------------------------------------
+# hierarchy and assignment
+# ---------------------------------------------------------------------------
+def _check_all(rs, ctx, cat, stride=3, f=0.7, min_n=10):
+    g = run_gpu_path(ctx, rs, cat, stride=stride, f=f, min_n=min_n)
+    o = run_oracle_path(cat, f=f, min_n=min_n)
+    assert np.array_equal(g["labels"], o["labels"])
+    assert np.array_equal(g["perm"], o["members"]) and np.array_equal(g["offsets"], o["offsets"])
+    gd, od = gpu_tree_dict(g["tree"]), oracle_tree_dict(o["tree"])
+    matched, excused = compare_trees(gd, od, cat.box)
+    info = g["tree"].info()
+    assert info.n_nodes == o["tree"].n_nodes or excused > 0
+    if excused == 0:
+        assert np.array_equal(g["halo_id"], o["halo_id"])
+        assert g["n_halos"] == len(o["halos"].id)
+    return matched, excused, info
+
+
+def test_refine_assign_c1(rs, ctx):
+    matched, excused, info = _check_all(rs, ctx, synth.generate("c1"))
+    assert matched > 50 and info.n_seeds > 30
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_refine_assign_small_catalogues(rs, ctx, seed):
+    _check_all(rs, ctx, _small(seed))
+
+
+def test_refine_stride4_and_f_values(rs, ctx):
+    c = _small(21)
+    _check_all(rs, ctx, c, stride=4)
+    _check_all(rs, ctx, c, f=0.5)
+    _check_all(rs, ctx, c, f=0.9, min_n=20)
+
+
+def test_refine_big_node_path(rs, ctx):
+    """Groups above 1024 members take the multi-CTA level path; their
+    children below it finish in the one-CTA subtree kernel."""
+    rng = np.random.default_rng(3)
+    box = 20.0
+    parts, vels = [], []
+    for k, n in enumerate((6000, 2500, 1500)):
+        centre = rng.random(3) * 14 + 3
+        p, v = synth.blob(rng, n, centre, rng.standard_normal(3) * 100, 0.15, 60.0)
+        parts.append(p)
+        vels.append(v)
+        # a co-spatial clump moving differently inside the first blob
+        if k == 0:
+            p2, v2 = synth.blob(rng, 800, centre, [300.0, 0, 0], 0.05, 30.0)
+            parts.append(p2)
+            vels.append(v2)
+    pos = synth.wrap(np.vstack(parts), box)
+    vel = np.vstack(vels).astype(np.float32)
+    n = len(pos)
+    perm = rng.permutation(n)
+    c = synth.Catalogue(pos=pos[perm].copy(), vel=vel[perm].copy(), box=box, truth=np.zeros(n, np.int32),
+                        comp_parent=np.zeros(0, np.int32), comp_n=np.zeros(0))
+    matched, excused, info = _check_all(rs, ctx, c)
+    assert info.n_levels >= 3
+
+
+def test_refine_group_across_box_corner(rs, ctx):
+    rng = np.random.default_rng(8)
+    box = 10.0
+    p, v = synth.blob(rng, 3000, [0.0, 0.0, 0.0], [0, 0, 0], 0.2, 50.0)
+    p2, v2 = synth.blob(rng, 400, [0.05, 9.95, 0.0], [200, 0, 0], 0.05, 20.0)
+    pos = synth.wrap(np.vstack([p, p2]), box)
+    vel = np.vstack([v, v2]).astype(np.float32)
+    n = len(pos)
+    c = synth.Catalogue(pos=pos, vel=vel, box=box, truth=np.zeros(n, np.int32), comp_parent=np.zeros(0, np.int32),
+                        comp_n=np.zeros(0))
+    _check_all(rs, ctx, c)
+
+
+def test_refine_duplicates(rs, ctx):
+    """Identical points: zero linking lengths and zero dispersions."""
+    rng = np.random.default_rng(4)
+    box = 10.0
+    base = rng.random((40, 3)) * 0.05 + 5.0
+    pos = synth.wrap(np.repeat(base, 30, axis=0), box)
+    vel = np.repeat(rng.standard_normal((40, 3)) * 10, 30, axis=0).astype(np.float32)
+    n = len(pos)
+    c = synth.Catalogue(pos=pos, vel=vel, box=box, truth=np.zeros(n, np.int32), comp_parent=np.zeros(0, np.int32),
+                        comp_n=np.zeros(0))
+    _check_all(rs, ctx, c)
+
+
+def test_level_labels(rs, ctx):
+    c = synth.generate("c1")
+    g = run_gpu_path(ctx, rs, c, assign=False)
+    o = run_oracle_path(c, assign=False)
+    t = g["tree"]
+    for level in range(t.info().n_levels):
+        assert np.array_equal(t.level_labels(level).cpu().numpy(), o["tree"].level_labels(level, c.n))
+
+
+def test_find_halos_host_and_device(rs, ctx):
+    c = _small(31)
+    o = run_oracle_path(c)
+    pos, vel = cuda_inputs(c)
+    lab = torch.empty(c.n, dtype=torch.int32, device="cuda")
+    hid, _, st = rs.rs_find_halos(ctx, pos, vel, c.box, fof_labels=lab)
+    assert np.array_equal(hid.cpu().numpy(), o["halo_id"])
+    assert np.array_equal(lab.cpu().numpy(), o["labels"])
+    hp = torch.from_numpy(c.pos).pin_memory()
+    vp = torch.from_numpy(c.vel).pin_memory()
+    hid2, _, st2 = rs.rs_find_halos(ctx, hp, vp, c.box)
+    assert not hid2.is_cuda
+    assert np.array_equal(hid2.numpy(), o["halo_id"])
+    assert st2["n_halos"] == len(o["halos"].id) == st["n_halos"]
+
+
+def test_empty_inputs(rs, ctx):
+    z = torch.zeros((0, 3), device="cuda")
+    hid, _, st = rs.rs_find_halos(ctx, z, z, 10.0)
+    assert hid.numel() == 0 and st["n_halos"] == 0
+    # a catalogue with no group of min_n members
+    c = synth.uniform(500, 10.0, 3)
+    g = run_gpu_path(ctx, rs, c)
+    assert g["tree"].info().n_nodes == 0 and np.all(g["halo_id"] == -1)
+
+
+def test_deterministic_repeat(rs, ctx):
+    c = _small(41)
+    a = run_gpu_path(ctx, rs, c)
+    b = run_gpu_path(ctx, rs, c)
+    assert np.array_equal(a["halo_id"], b["halo_id"])
+    assert gpu_tree_dict(a["tree"]).keys() == gpu_tree_dict(b["tree"]).keys()
+
+
+@pytest.mark.slow
+def test_full_path_c2(rs, ctx):
+    matched, excused, info = _check_all(rs, ctx, synth.generate("c2"))
+    print(f"c2: nodes {info.n_nodes} matched {matched} excused {excused} tie {info.n_tieband}")
