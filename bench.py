@@ -1,0 +1,326 @@
+"""Benchmark of the ROCKSTAR hot path on GB300: particles/s through 3D FOF,
+the 6D phase-space hierarchy and seed assignment.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config c3] [--impl ours|reference]
+
+One step = rs_fof3d + rs_group_sort + rs_refine6d + rs_assign over one
+synthetic catalogue resident in HBM.  With N > 1 (torchrun, one process per
+GPU) every rank runs an independent replica of the workload ("replicas
+only": the catalogue is not partitioned); value = all ranks' particles
+divided by the slowest rank's time.  Prints one JSON line on rank 0.
+
+``--impl reference`` times the float64 CPU oracle instead, on bounded
+samples of the same workload (sub-cubes of the box), on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1110_4372_gb300 import synth  # noqa: E402
+
+WORKLOADS = {
+    "c1": "32^3=32768 particles, L=10 Mpc/h, 40 NFW halos of 20-4000 particles (dN/dn ~ n^-1.9), uniform background",
+    "c2": "128^3=2097152 particles, L=40 Mpc/h, 2500 NFW halos of 20-200k particles with 1-8 subhalos each",
+    "c3": "512^3=134217728 particles, L=160 Mpc/h, 150k NFW halos of 20-10^6 particles, subhalos and "
+          "sub-subhalos, uniform background; plain 3D FOF b=0.28, 6D refinement f=0.7, min 10 particles",
+    "c5": "1024^3=1073741824 particles, L=320 Mpc/h, 1.2M NFW halos of 20-10^6 particles, subhalos and sub-subhalos",
+    "c3q": "256^3=16777216 particles, L=80 Mpc/h, 18750 NFW halos of 20-10^6 particles with subhalos "
+           "(the 134M workload at 1/8 of its volume; profiling size)",
+}
+METRIC = "particles/s through 3D FOF + 6D refinement at 134M particles; HBM roofline fraction"
+
+# Algorithmic bytes per unit (the strict minimum each step moves): a 3D FOF
+# particle reads 12 B of position and writes a 4 B label; a member of a node
+# at one refinement level reads 24 B of position and velocity and writes a
+# 4 B label; assignment reads 24 B and writes 4 B per grouped particle.
+BYTES_FOF_PER_PARTICLE = 16
+BYTES_LEVEL_PER_MEMBER = 28
+BYTES_ASSIGN_PER_MEMBER = 28
+
+# Which units each kernel processes per step (for its algorithmic bytes).
+KERNEL_UNITS = {
+    "fof_link": ("particles", BYTES_FOF_PER_PARTICLE),
+    "fof_keys": ("particles", BYTES_FOF_PER_PARTICLE),
+    "rf_small_subtree": ("small_level_members", BYTES_LEVEL_PER_MEMBER),
+    "rf_lvl_nn": ("big_level_members", BYTES_LEVEL_PER_MEMBER),
+    "rf_lvl_link": ("big_level_members", BYTES_LEVEL_PER_MEMBER),
+    "as_assign": ("members", BYTES_ASSIGN_PER_MEMBER),
+}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.tmp,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.split(",") for r in self.tmp.read().strip().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if r[5 + k].lower() in ("active", "0x1", "1"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def sub_cube(cat, frac_side: float):
+    """Particles of the catalogue inside [0, box*frac_side)^3 (a bounded
+    sample of the same workload for the CPU oracle)."""
+    s = cat.box * frac_side
+    m = np.all(cat.pos < s, axis=1)
+    return cat.pos[m].copy(), cat.vel[m].copy()
+
+
+def time_oracle_sample(cat, frac_side: float):
+    import oracle
+    pos, vel = sub_cube(cat, frac_side)
+    # the linking length of the full catalogue
+    l = oracle.linking_length(cat.n, cat.box, 0.28)
+    t0 = time.perf_counter()
+    lab, _, _ = oracle.fof3d(pos, cat.box, l=l)
+    mem, off = oracle.groups_from_labels(lab, 10)
+    tree = oracle.refine(pos, vel, cat.box, mem, off, 0.7, 10)
+    oracle.assign(tree, len(pos), cat.box, 360.0, cat.n / cat.box ** 3)
+    return len(pos), time.perf_counter() - t0
+
+
+def reference_arm(args, cat, cfg_json):
+    """The oracle, as it stands, on host cores: each step one bounded sample."""
+    side = args.ref_side
+    for _ in range(args.warmup):
+        time_oracle_sample(cat, side)
+    tot_p, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        p, t = time_oracle_sample(cat, side)
+        tot_p += p
+        tot_t += t
+    v = tot_p / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "particles/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": cfg_json,
+            "cpu_baseline": {"value": v, "unit": "particles/s", "cores": 1, "kind": "oracle",
+                             "sample": f"particles in the sub-cube [0, {side:g} L)^3 of the workload "
+                                       f"({tot_p // max(args.steps, 1)} per step): 3D FOF + refinement + "
+                                       f"assignment, float64 C oracle, single thread"},
+            "e2e": {"value": v, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-side", type=float, default=1.0 / 6.0, help="sub-cube side for the CPU baseline")
+    ap.add_argument("--ref-side", type=float, default=1.0 / 8.0, help="sub-cube side per reference step")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    cfg = synth.CONFIGS[args.config]
+    cfg_json = {"workload": WORKLOADS[args.config], "name": args.config, "particles": cfg["n"], "box": cfg["box"],
+                "b": 0.28, "f": 0.7, "min_n": 10, "parallelism": "replicas" if world > 1 else "single",
+                "l2": "inputs larger than L2 (pos+vel 24 B/particle)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cat = synth.generate(args.config)
+        reference_arm(args, cat, cfg_json)
+        return
+
+    import torch
+    from paper_1110_4372_gb300 import rsgpu
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    cat = synth.generate(args.config)
+    n = cat.n
+    ctx = rsgpu.Context()
+    pos = torch.from_numpy(cat.pos).cuda()
+    vel = torch.from_numpy(cat.vel).cuda()
+    halo = torch.empty(n, dtype=torch.int32, device="cuda")
+    p = rsgpu.params()
+
+    def step():
+        _, _, st = rsgpu.rs_find_halos(ctx, pos, vel, cat.box, p, halo_id=halo)
+        return st
+
+    for _ in range(max(args.warmup, 0)):
+        stats = step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    rsgpu.rs_profile_reset(ctx)
+    rsgpu.rs_profile_enable(ctx, True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        stats = step()
+    ev1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    rsgpu.rs_profile_enable(ctx, False)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = rsgpu.rs_profile_read(ctx)
+    launches = rsgpu.rs_launch_count(ctx) // max(args.steps, 1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n / (ms * 1e-3)
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.from_numpy(cat.pos).pin_memory()
+        hv = torch.from_numpy(cat.vel).pin_memory()
+        hout = torch.empty(n, dtype=torch.int32).pin_memory()
+        rsgpu.rs_find_halos(ctx, hp, hv, cat.box, p, halo_id=hout)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        k = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(k):
+            rsgpu.rs_find_halos(ctx, hp, hv, cat.box, p, halo_id=hout)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / k
+        if dist:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * n / dt, "unit": "particles/s", "h2d_bytes_per_step": 2 * 12 * n,
+               "d2h_bytes_per_step": 4 * n, "ms_per_step": 1e3 * dt}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel ----
+    peaks, peak_kind = load_peaks()
+    total_ms = sum(v[1] for v in prof.values())
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_launches, dom_ms) = dom
+    units = {"particles": n, "members": stats["n_members"], "level_members": stats["sum_level_members"],
+             "big_level_members": stats["sum_big_level_members"],
+             "small_level_members": stats["sum_level_members"] - stats["sum_big_level_members"]}
+    unit_name, per_unit = KERNEL_UNITS.get(dom_name, ("level_members", BYTES_LEVEL_PER_MEMBER))
+    bytes_per_step = per_unit * units[unit_name]
+    achieved = bytes_per_step * args.steps / (dom_ms * 1e-3) / 1e9
+    peak = peaks["hbm_gbs"]
+    roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_kind": f"{peak_kind} (hbm_gbs)",
+                "algorithmic_bytes_per_step": bytes_per_step, "unit_per_step": f"{units[unit_name]} {unit_name}",
+                "ms_per_step": dom_ms / args.steps, "share": dom_ms / total_ms if total_ms else None}
+    b_alg = BYTES_FOF_PER_PARTICLE * n + BYTES_LEVEL_PER_MEMBER * stats["sum_level_members"]
+    path_frac = b_alg / (ms * 1e-3) / 1e9 / peak
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        npart, t = time_oracle_sample(cat, args.cpu_side)
+        cpu = {"value": npart / t, "unit": "particles/s", "cores": 1, "kind": "oracle",
+               "sample": f"{npart} particles in the sub-cube [0, {args.cpu_side:.4g} L)^3 of the workload: "
+                         f"3D FOF + refinement + assignment, float64 C oracle, single thread, {t:.1f} s"}
+
+    stages = {}
+    for k, (cnt, t) in prof.items():
+        stage = k.split("_")[0]
+        stages[stage] = stages.get(stage, 0.0) + t / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg_json,
+        "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clocks, "roofline": roofline,
+        "cpu_baseline": cpu,
+        "path_hbm_frac": path_frac, "b_alg_bytes_per_step": b_alg,
+        "stage_ms": {k: round(v, 3) for k, v in sorted(stages.items(), key=lambda kv: -kv[1])},
+        "top_kernels_ms": {k: round(v[1] / args.steps, 3) for k, v in
+                           sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]},
+        "stats": stats,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

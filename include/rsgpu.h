@@ -181,6 +181,8 @@ typedef struct {
     int64_t n_halos;
     int64_t n_tieband6d;
     int64_t sum_level_members; /* members summed over all nodes (for byte counts) */
+    int64_t sum_big_level_members; /* the part of it processed by the multi-block level path */
+    int32_t n_fallback_levels;     /* big-node levels whose sampled search radius did not hold */
 } rs_stats;
 
 /* rs_fof3d + rs_group_sort + rs_refine6d + rs_assign.  With host_buffers =

@@ -48,6 +48,8 @@ extern "C" rs_status rs_find_halos(rs_ctx *ctx, const float *pos, const float *v
             stats->n_halos = H;
             stats->n_tieband6d = tree->n_tieband;
             stats->sum_level_members = tree->sum_level_members;
+            stats->sum_big_level_members = tree->sum_big_level_members;
+            stats->n_fallback_levels = tree->n_fallback_levels;
         }
         const size_t ob = sizeof(int32_t) * (size_t)n;
         if (host_buffers) {

@@ -277,14 +277,7 @@ __global__ void __launch_bounds__(AS_THREADS) k_as_rdyn(AsBufs A, int n_halos, c
                 if (rr > 0) best = fmax(best, __ddiv_rn((double)(m + 1), rr));
             }
         } else {
-            // large halo: rank of each radius by counting
-            for (unsigned long long m = threadIdx.x; m < s; m += AS_THREADS) {
-                const double rm = radius(m);
-                if (!(rm > 0)) continue;
-                unsigned long long rank = 0;
-                for (unsigned long long j = 0; j < s; j++) rank += radius(j) <= rm ? 1ull : 0ull;
-                best = fmax(best, __ddiv_rn((double)rank, rm));
-            }
+            continue;  // large halo: handled by the sort-based kernels below
         }
         best = warp_max(best);
         if (lane_id() == 0) wbest[warp_id()] = best;
@@ -301,6 +294,89 @@ __global__ void __launch_bounds__(AS_THREADS) k_as_rdyn(AsBufs A, int n_halos, c
         }
         __syncthreads();
     }
+}
+
+// ---- r_dyn of halos above RDYN_SMEM_N members: one global sort ----
+// Members of large halos get keys (large-halo rank, float32 radius) -- float32
+// rounding is monotone, so the order is the float64 order up to runs of
+// equal float32 keys, inside which each member's exact float64 rank is
+// counted directly.  max_k k / r_(k) is then taken per halo with a 64-bit
+// atomic max on the (positive) double's bits.
+__global__ void k_as_large_flag(int n_halos, const unsigned long long *hoff, unsigned *lflag)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_halos) return;
+    lflag[k] = (hoff[k + 1] - hoff[k]) > (unsigned long long)RDYN_SMEM_N ? 1u : 0u;
+}
+
+__global__ void k_as_large_size(int n_halos, const unsigned long long *hoff, const unsigned *lflag,
+                                const unsigned *lscan, long long *lsize, int *lhalo)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_halos || !lflag[k]) return;
+    lsize[lscan[k]] = (long long)(hoff[k + 1] - hoff[k]);
+    lhalo[lscan[k]] = k;
+}
+
+__global__ void k_as_large_keys(int nlarge, const long long *loff, const int *lhalo, const int *root_of_rank,
+                                const unsigned long long *hoff, const int *hmem, const int *members, const float *pos,
+                                int stride, double box, AsBufs A, unsigned long long *keys, unsigned *vals,
+                                double *r64)
+{
+    for (int li = blockIdx.x; li < nlarge; li += gridDim.x) {
+        const int k = lhalo[li];
+        const int r = root_of_rank[k];
+        const unsigned long long a0 = hoff[k], s = hoff[k + 1] - hoff[k];
+        const long long o = loff[li];
+        for (unsigned long long m = threadIdx.x; m < s; m += blockDim.x) {
+            const int i = members[hmem[a0 + m]];
+            const float *p = pos + (int64_t)stride * i;
+            double acc = 0.0;
+            for (int d = 0; d < 3; d++) {
+                double dx = min_image64(f64_sub((double)p[d], A.hx[3 * r + d]), box);
+                acc = f64_add(acc, f64_mul(dx, dx));
+            }
+            const double rr = sqrt(acc);
+            r64[o + m] = rr;
+            keys[o + m] = ((unsigned long long)li << 32) | __float_as_uint((float)rr);
+            vals[o + m] = (unsigned)(o + m);
+        }
+    }
+}
+
+__global__ void k_as_large_max(long long total, const long long *loff, const unsigned long long *keys,
+                               const unsigned *vals, const double *r64, unsigned long long *best_bits)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const unsigned long long key = keys[t];
+    const int li = (int)(key >> 32);
+    const long long start = loff[li];
+    const double r = r64[vals[t]];
+    if (!(r > 0)) return;
+    // bounds of the run of equal keys holding t
+    long long a = t, b = t + 1;
+    while (a > start && keys[a - 1] == key) a--;
+    while (b < total && keys[b] == key) b++;
+    long long rank = a - start;
+    for (long long u = a; u < b; u++) rank += r64[vals[u]] <= r ? 1 : 0;
+    const double v = __ddiv_rn((double)rank, r);
+    atomicMax(&best_bits[li], (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void k_as_large_fin(int nlarge, const int *lhalo, const int *root_of_rank,
+                               const unsigned long long *best_bits, AsBufs A, double rho_term)
+{
+    int li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= nlarge) return;
+    const int r = root_of_rank[lhalo[li]];
+    const double b = __longlong_as_double((long long)best_bits[li]);
+    const double r2 = __ddiv_rn(b, rho_term);
+    A.hrdyn2[r] = r2;
+    const double sv2 = f64_mul(A.hsigv[r], A.hsigv[r]);
+    float *f = A.hfast + 16 * (int64_t)r;
+    f[12] = r2 > 0 ? (float)(1.0 / r2) : -1.f;
+    f[13] = sv2 > 0 ? (float)(1.0 / sv2) : -1.f;
 }
 
 __global__ void k_as_tiles_prep(NodeArrays nd, int nn, const int *span, int64_t *tiles)
@@ -332,12 +408,34 @@ __device__ __forceinline__ int lower_bound_u32(const unsigned *a, int n, unsigne
     return lo;
 }
 
-__global__ void __launch_bounds__(AS_THREADS) k_as_assign(AsBufs A, NodeArrays nd, const int *tnode, const int *tq0,
-                                                          const int *members, const float *pos, const float *vel,
-                                                          int stride, double box, float boxf, int32_t *halo_id,
+constexpr int AS_CAND = 4096;  // seeds deduplicated in shared memory per node
+
+__global__ void k_as_leafroot(AsBufs A, int *leaf_root, rs_dev_status *st)
+{
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= A.L) return;
+    leaf_root[a] = uf_find(A.uf, a, st);
+}
+
+__device__ __forceinline__ float as_d2_32(float4 p, float4 v, const float *f)
+{
+    float dx = (p.x - f[0]) - f[3], dy = (p.y - f[1]) - f[4], dz = (p.z - f[2]) - f[5];
+    float ux = (v.x - f[6]) - f[9], uy = (v.y - f[7]) - f[10], uz = (v.z - f[8]) - f[11];
+    return (dx * dx + dy * dy + dz * dz) * f[12] + (ux * ux + uy * uy + uz * uz) * f[13];
+}
+
+// One block per tile of a node's own members (those outside its children).
+// The node's seeds are the seed-list run [la, lb); their halos are
+// deduplicated in shared memory, then each member takes the only halo or the
+// Eq. 3 nearest one (float32 pass, float64 over the float32 band).
+__global__ void __launch_bounds__(AS_THREADS) k_as_assign(AsBufs A, NodeArrays nd, const int *leaf_root,
+                                                          const int *tnode, const int *tq0, const int *members,
+                                                          const float *pos, const float *vel, int stride,
+                                                          double box, float boxf, int32_t *halo_id,
                                                           rs_dev_status *st)
 {
-    __shared__ int s_la, s_lb, s_r0;
+    __shared__ int cand[AS_CAND];
+    __shared__ int s_la, s_lb, s_nc;
     const int node = tnode[blockIdx.x];
     const int q0 = tq0[blockIdx.x];
     const int first = nd.first[node], cnt = nd.count[node];
@@ -345,57 +443,76 @@ __global__ void __launch_bounds__(AS_THREADS) k_as_assign(AsBufs A, NodeArrays n
     if (threadIdx.x == 0) {
         s_la = lower_bound_u32(A.leaf_first, A.L, (unsigned)first);
         s_lb = lower_bound_u32(A.leaf_first, A.L, (unsigned)(first + cnt));
-        s_r0 = s_la < s_lb ? uf_find(A.uf, s_la, st) : -1;
     }
     __syncthreads();
-    const int la = s_la, lb = s_lb, r0 = s_r0;
-    bool single = true;
-    for (int b = la + threadIdx.x; b < lb; b += AS_THREADS)
-        if (uf_find(A.uf, b, st) != r0) single = false;
-    single = __syncthreads_and(single);
+    const int la = s_la, lb = s_lb;
+    const int nl = lb - la;
+    const bool staged = nl <= AS_CAND;
+    int nc = nl;
+    const int *cl = leaf_root + la;  // candidate halo roots (possibly repeated)
+    if (staged) {
+        int P = 1;
+        while (P < nl) P <<= 1;
+        for (int i = threadIdx.x; i < P; i += AS_THREADS) cand[i] = i < nl ? leaf_root[la + i] : 0x7fffffff;
+        __syncthreads();
+        for (int kk = 2; kk <= P; kk <<= 1)
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                for (int t = threadIdx.x; t < P / 2; t += AS_THREADS) {
+                    int i = 2 * j * (t / j) + (t % j), l = i + j;
+                    bool up = (i & kk) == 0;
+                    int x = cand[i], y = cand[l];
+                    if ((x > y) == up) {
+                        cand[i] = y;
+                        cand[l] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        // unique, in place, by one thread (nl <= 4096)
+        if (threadIdx.x == 0) {
+            int u = 0;
+            for (int i = 0; i < nl; i++)
+                if (i == 0 || cand[i] != cand[i - 1]) cand[u++] = cand[i];
+            s_nc = u;
+        }
+        __syncthreads();
+        nc = s_nc;
+        cl = cand;
+    }
     const int m = tail0 + q0 + threadIdx.x;
     if (m >= first + cnt) return;
     const int i = members[m];
-    if (r0 < 0) {
+    if (nl <= 0) {
         dev_fail(st, DEV_INTERNAL, 60, node);
         return;
     }
-    if (single) {
-        halo_id[i] = A.hid[r0];
+    if (nc == 1) {
+        halo_id[i] = A.hid[cl[0]];
         return;
     }
     const float4 p = unwrap_pos(pos, stride, i, nd.shift[node], boxf);
     const float4 v = load_vel(vel, stride, i);
-    // float32 pass
     float best = INFINITY;
     bool need64 = false;
-    for (int b = la; b < lb; b++) {
-        const int r = uf_find(A.uf, b, st);
-        const float *f = A.hfast + 16 * (int64_t)r;
+    for (int c = 0; c < nc; c++) {
+        const float *f = A.hfast + 16 * (int64_t)cl[c];
         if (f[12] < 0.f || f[13] < 0.f) {
             need64 = true;
             continue;
         }
-        float dx = (p.x - f[0]) - f[3], dy = (p.y - f[1]) - f[4], dz = (p.z - f[2]) - f[5];
-        float ux = (v.x - f[6]) - f[9], uy = (v.y - f[7]) - f[10], uz = (v.z - f[8]) - f[11];
-        float d2 = (dx * dx + dy * dy + dz * dz) * f[12] + (ux * ux + uy * uy + uz * uz) * f[13];
-        best = fminf(best, d2);
+        best = fminf(best, as_d2_32(p, v, f));
     }
     const float lim = best * (float)(1.0 + 2.0 * RS_BAND);
-    // float64 over the band (and any halo with a zero denominator)
     double b64 = INFINITY;
     int bid = 0x7fffffff;
     const float *pr = pos + (int64_t)stride * i;
     const float *vr = vel + (int64_t)stride * i;
-    for (int b = la; b < lb; b++) {
-        const int r = uf_find(A.uf, b, st);
+    for (int c = 0; c < nc; c++) {
+        const int r = cl[c];
         const float *f = A.hfast + 16 * (int64_t)r;
         const bool zero = f[12] < 0.f || f[13] < 0.f;
         if (!zero) {
-            float dx = (p.x - f[0]) - f[3], dy = (p.y - f[1]) - f[4], dz = (p.z - f[2]) - f[5];
-            float ux = (v.x - f[6]) - f[9], uy = (v.y - f[7]) - f[10], uz = (v.z - f[8]) - f[11];
-            float d2 = (dx * dx + dy * dy + dz * dz) * f[12] + (ux * ux + uy * uy + uz * uz) * f[13];
-            if (d2 > lim) continue;
+            if (as_d2_32(p, v, f) > lim) continue;
         } else if (!need64) {
             continue;
         }
@@ -437,6 +554,50 @@ T *carve(char *&p, int64_t count)
     size_t b = sizeof(T) * (size_t)(count > 0 ? count : 1);
     p += (b + 255) / 256 * 256;
     return r;
+}
+
+rs_status large_rdyn(rs_ctx *ctx, AsBufs A, int H, const int *root_of_rank, const unsigned long long *hoff,
+                     const int *hmem, const int *members, const float *pos, int stride, double box, double rho_term)
+{
+    if (H == 0) return RS_OK;
+    RS_WS(ctx, unsigned, lfl, WS_RF_MISC0, 2 * (int64_t)H + 8);
+    unsigned *lflag = lfl, *lscan = lfl + H, *ltot = lfl + 2 * H;
+    RS_LAUNCH(ctx, "as_large_flag", k_as_large_flag, ceil_div(H, 256), 256, 0, H, hoff, lflag);
+    RS_CUDA(ctx, cudaMemcpyAsync(lscan, lflag, sizeof(unsigned) * H, cudaMemcpyDeviceToDevice, ctx->stream));
+    RS_TRY(rs_scan_u32(ctx, lscan, H, ltot));
+    RS_CUDA(ctx, cudaMemcpyAsync(ctx->h_scratch, ltot, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    RS_TRY(rs_sync_check(ctx, "rs_assign"));
+    const int NL = (int)(*(unsigned *)ctx->h_scratch);
+    if (NL == 0) return RS_OK;
+    RS_WS(ctx, long long, lo, WS_RF_MISC1, 2 * (int64_t)NL + 8);
+    long long *lsize = lo, *ltot2 = lo + NL + 1;
+    int *lhalo = (int *)(lo + NL + 4);
+    RS_CUDA(ctx, cudaMemsetAsync(lsize + NL, 0, sizeof(long long), ctx->stream));
+    RS_LAUNCH(ctx, "as_large_size", k_as_large_size, ceil_div(H, 256), 256, 0, H, hoff, (const unsigned *)lflag,
+              (const unsigned *)lscan, lsize, lhalo);
+    RS_TRY(rs_scan_i64(ctx, (int64_t *)lsize, NL + 1, (int64_t *)ltot2));
+    int64_t total;
+    RS_TRY(rs_read_i64(ctx, lsize + NL, 1, &total, "rs_assign"));
+    RS_WS(ctx, uint64_t, k0, WS_SORT_K0, total);
+    RS_WS(ctx, uint64_t, k1, WS_SORT_K1, total);
+    RS_WS(ctx, uint32_t, v0, WS_SORT_V0, total);
+    RS_WS(ctx, uint32_t, v1, WS_SORT_V1, total);
+    RS_WS(ctx, double, r64, WS_RF_DNN, total);
+    RS_WS(ctx, unsigned long long, bb, WS_RF_MISC2, NL);
+    RS_CUDA(ctx, cudaMemsetAsync(bb, 0, sizeof(unsigned long long) * NL, ctx->stream));
+    RS_LAUNCH(ctx, "as_large_keys", k_as_large_keys, std::min<int64_t>(NL, (int64_t)ctx->num_sms * 4), 256, 0, NL,
+              (const long long *)lsize, (const int *)lhalo, root_of_rank, hoff, hmem, members, pos, stride, box, A,
+              (unsigned long long *)k0, v0, r64);
+    int bits = 32;
+    while (bits < 64 && ((uint64_t)(NL - 1) >> (bits - 32)) != 0) bits++;
+    bool alt = false;
+    RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, total, bits, &alt));
+    RS_LAUNCH(ctx, "as_large_max", k_as_large_max, ceil_div(total, 256), 256, 0, (long long)total,
+              (const long long *)lsize, (const unsigned long long *)(alt ? k1 : k0), (const unsigned *)(alt ? v1 : v0),
+              (const double *)r64, bb);
+    RS_LAUNCH(ctx, "as_large_fin", k_as_large_fin, ceil_div(NL, 256), 256, 0, NL, (const int *)lhalo, root_of_rank,
+              (const unsigned long long *)bb, A, rho_term);
+    return RS_OK;
 }
 
 }  // namespace
@@ -514,6 +675,8 @@ extern "C" rs_status rs_assign(rs_ctx *ctx, const rs_tree *t, const float *pos, 
     RS_LAUNCH(ctx, "as_merge", k_as_merge, gl, 256, 0, A, nd, box, params->merge_thresh, ctx->d_status);
     RS_LAUNCH(ctx, "as_roots", k_as_roots, gl, 256, 0, A, nd, (const int *)t->members, pos, vel, stride, boxf,
               ctx->d_status);
+    RS_WS(ctx, int, leaf_root, WS_AS_7, L);
+    RS_LAUNCH(ctx, "as_leafroot", k_as_leafroot, gl, 256, 0, A, leaf_root, ctx->d_status);
     const int64_t gblk = std::min<int64_t>(L, (int64_t)ctx->num_sms * 8);
     RS_LAUNCH(ctx, "as_hmom", k_as_hmom, gblk, AS_THREADS, 0, A, nd, (const int *)t->members, pos, vel, stride, boxf,
               ctx->d_status);
@@ -543,6 +706,9 @@ extern "C" rs_status rs_assign(rs_ctx *ctx, const rs_tree *t, const float *pos, 
     RS_LAUNCH(ctx, "as_rdyn", k_as_rdyn, std::min<int64_t>(H, (int64_t)ctx->num_sms * 8), AS_THREADS, 0, A, (int)H,
               (const int *)root_of_rank, (const unsigned long long *)hoff, (const int *)hmem,
               (const int *)t->members, pos, stride, box, rho_term);
+    // r_dyn of the halos too large for one block's shared memory
+    RS_TRY(large_rdyn(ctx, A, (int)H, (const int *)root_of_rank, (const unsigned long long *)hoff, (const int *)hmem,
+                      (const int *)t->members, pos, stride, box, rho_term));
     // assignment tiles over every node's own members (outside its children)
     RS_WS(ctx, int64_t, tl, WS_RF_MISC1, (int64_t)nn + 8);
     RS_LAUNCH(ctx, "as_tiles_prep", k_as_tiles_prep, ceil_div(nn, 256), 256, 0, nd, nn, (const int *)span, tl);
@@ -553,7 +719,8 @@ extern "C" rs_status rs_assign(rs_ctx *ctx, const rs_tree *t, const float *pos, 
     RS_WS(ctx, int, tt, WS_RF_MISC2, 2 * T + 8);
     RS_LAUNCH(ctx, "as_tiles_fill", k_as_tiles_fill, std::min<int64_t>(nn, 65535), 128, 0, nn, (const int64_t *)tl, tt,
               tt + T);
-    RS_LAUNCH(ctx, "as_assign", k_as_assign, T, AS_THREADS, 0, A, nd, (const int *)tt, (const int *)(tt + T),
+    RS_LAUNCH(ctx, "as_assign", k_as_assign, T, AS_THREADS, 0, A, nd, (const int *)leaf_root, (const int *)tt,
+              (const int *)(tt + T),
               (const int *)t->members, pos, vel, stride, box, boxf, halo_id, ctx->d_status);
     if (n_halos) {
         *n_halos = H;

@@ -167,11 +167,15 @@ __device__ __forceinline__ int pair_link(const float4 &pa, const float4 &pb, int
 }
 
 // One thread per fine cell: join it with every fine cell of larger index
-// within two fine cells per axis that has a friend pair with it.
+// within two fine cells per axis that has a friend pair with it.  Pass 0
+// takes the 26 adjacent cells (offsets of at most 1 per axis), where pairs are
+// friends almost at once in dense regions; pass 1 takes the cells two apart
+// on some axis, by which time dense regions are mostly one set and the
+// same-set check skips them.
 __global__ void __launch_bounds__(FOF_THREADS) k_fof_link(int64_t n_cells_cap, const uint32_t *n_cells_p,
                                                             const uint64_t *cell_key, const uint32_t *cell_start,
                                                             const uint32_t *table, const float4 *spos, int *parent,
-                                                            FofGeom g, rs_dev_status *st)
+                                                            FofGeom g, int pass, rs_dev_status *st)
 {
     const int64_t M = *n_cells_p;
     for (int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; A < M; A += (int64_t)gridDim.x * blockDim.x) {
@@ -201,6 +205,8 @@ __global__ void __launch_bounds__(FOF_THREADS) k_fof_link(int64_t n_cells_cap, c
                         int ox = fine_offset(ax, bx, g.Gf, sx), oy = fine_offset(ay, by, g.Gf, sy),
                             oz = fine_offset(az, bz, g.Gf, sz);
                         if (ox < -2 || ox > 2 || oy < -2 || oy > 2 || oz < -2 || oz > 2) continue;
+                        const bool adjacent = ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1;
+                        if (adjacent != (pass == 0)) continue;
                         if (uf_find(parent, (int)A, st) == uf_find(parent, (int)B, st)) continue;
                         const uint32_t b0 = cell_start[B], b1 = cell_start[B + 1];
                         bool linked = false;
@@ -392,9 +398,10 @@ extern "C" rs_status rs_fof3d(rs_ctx *ctx, const float *pos, int32_t stride, int
     RS_LAUNCH(ctx, "fof_fill", k_fill_u32, std::min<int64_t>(nb, (int64_t)ctx->num_sms * 16), T, 0,
               (uint32_t *)root_min, n, 0x7fffffffu);
     const int64_t grid = std::min<int64_t>(nb, (int64_t)ctx->num_sms * 32);
-    RS_LAUNCH(ctx, "fof_link", k_fof_link, grid, T, 0, n, (const uint32_t *)n_cells, (const uint64_t *)cell_key,
-              (const uint32_t *)cell_start, (const uint32_t *)table, (const float4 *)spos, parent, g,
-              ctx->d_status);
+    for (int pass = 0; pass < 2; pass++)
+        RS_LAUNCH(ctx, "fof_link", k_fof_link, grid, T, 0, n, (const uint32_t *)n_cells, (const uint64_t *)cell_key,
+                  (const uint32_t *)cell_start, (const uint32_t *)table, (const float4 *)spos, parent, g, pass,
+                  ctx->d_status);
     RS_LAUNCH(ctx, "fof_rootmin", k_fof_rootmin, grid, T, 0, (const uint32_t *)n_cells,
               (const uint32_t *)cell_start, (const uint32_t *)idx, parent, root_min, ctx->d_status);
     RS_LAUNCH(ctx, "fof_labels", k_fof_labels, nb, T, 0, n, (const uint32_t *)idx, (const uint32_t *)cell_of,

@@ -149,6 +149,10 @@ __global__ void k_make_roots(int64_t G, const int64_t *off, const int *gmin, con
     if (g >= G) return;
     int64_t cnt = off[g + 1] - off[g];
     if (cnt < min_n) return;
+    if (cnt > ((int64_t)8 << 23)) {  // the per-node hierarchy has at most 24 levels
+        dev_fail(st, DEV_OVERFLOW, 35, g);
+        return;
+    }
     int id = atomicAdd(nd.counter, 1);
     if (id >= nd.cap) {
         dev_fail(st, DEV_OVERFLOW, 31, id);
@@ -557,35 +561,582 @@ __global__ void k_lvl_finalize(LevelBufs L, NodeArrays nd, double box)
     L.met[k] = metric_of(o.sigx, o.sigv);
 }
 
-// brute-force nearest neighbour over the node, candidates staged in smem
-__global__ void __launch_bounds__(TQ) k_lvl_nn(LevelBufs L, NodeArrays nd, const float4 *wpos, const float4 *wvel,
-                                               float *dnn)
+// ---- buckets of 32 members, super-buckets of 32 buckets, raw-coordinate boxes ----
+// A box is (lo, hi) over the six raw float32 coordinates of its members (the
+// unwrapped positions and the velocities).  The gap between two boxes along
+// an axis is one float32 subtraction of exact input values, so the box
+// distance below is within 8 float32 ulps (relative) of the exact minimum
+// squared distance between the boxes under the node's metric; a box is
+// skipped only when that bound exceeds the current radius by 2^-18 relative,
+// which can never skip a member whose float32 distance would change the
+// result.
+#define RS_PRUNE_SLACK 1.000003814697265625f  // 1 + 2^-18
+
+struct Box6 {
+    float4 plo, phi, vlo, vhi;
+};
+
+// ---- per-node bounding-volume hierarchy over the member range ----
+// Leaves hold BVH_LEAF consecutive members (the range is in 6D Morton order);
+// box (h, i) of level h covers leaves [i 2^h, (i+1) 2^h) and is the union of
+// boxes (h-1, 2i) and (h-1, 2i+1).  Boxes of a node are stored level by
+// level starting at its base offset.
+constexpr int BVH_LEAF = 32;
+constexpr int BVH_STACK = 40;
+
+__device__ __forceinline__ int bvh_count(int nl, int h) { return (nl + (1 << h) - 1) >> h; }
+
+__device__ __forceinline__ int bvh_levels(int nl)
 {
-    __shared__ float4 cp[TQ], cv[TQ];
-    const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x];
+    int h = 0;
+    while (bvh_count(nl, h) > 1) h++;
+    return h + 1;
+}
+
+__device__ __forceinline__ int64_t bvh_total(int nl)
+{
+    int64_t t = 0;
+    const int H = bvh_levels(nl);
+    for (int h = 0; h < H; h++) t += bvh_count(nl, h);
+    return t;
+}
+
+__global__ void k_bvh_prep(const int *list, int K, NodeArrays nd, int64_t *nbox)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const int n = nd.count[list[k]];
+    nbox[k] = bvh_total((int)ceil_div(n, BVH_LEAF));
+}
+
+__device__ __forceinline__ Box6 box_empty()
+{
+    Box6 b;
+    b.plo = b.vlo = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+    b.phi = b.vhi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+    return b;
+}
+
+__device__ __forceinline__ void box_add(Box6 &b, float4 p, float4 v)
+{
+    b.plo.x = fminf(b.plo.x, p.x); b.plo.y = fminf(b.plo.y, p.y); b.plo.z = fminf(b.plo.z, p.z);
+    b.phi.x = fmaxf(b.phi.x, p.x); b.phi.y = fmaxf(b.phi.y, p.y); b.phi.z = fmaxf(b.phi.z, p.z);
+    b.vlo.x = fminf(b.vlo.x, v.x); b.vlo.y = fminf(b.vlo.y, v.y); b.vlo.z = fminf(b.vlo.z, v.z);
+    b.vhi.x = fmaxf(b.vhi.x, v.x); b.vhi.y = fmaxf(b.vhi.y, v.y); b.vhi.z = fmaxf(b.vhi.z, v.z);
+}
+
+__device__ __forceinline__ Box6 box_union(const Box6 &a, const Box6 &c)
+{
+    Box6 b;
+    b.plo = make_float4(fminf(a.plo.x, c.plo.x), fminf(a.plo.y, c.plo.y), fminf(a.plo.z, c.plo.z), 0.f);
+    b.phi = make_float4(fmaxf(a.phi.x, c.phi.x), fmaxf(a.phi.y, c.phi.y), fmaxf(a.phi.z, c.phi.z), 0.f);
+    b.vlo = make_float4(fminf(a.vlo.x, c.vlo.x), fminf(a.vlo.y, c.vlo.y), fminf(a.vlo.z, c.vlo.z), 0.f);
+    b.vhi = make_float4(fmaxf(a.vhi.x, c.vhi.x), fmaxf(a.vhi.y, c.vhi.y), fmaxf(a.vhi.z, c.vhi.z), 0.f);
+    return b;
+}
+
+// one block builds one node's hierarchy, level by level
+__global__ void __launch_bounds__(256) k_bvh_build(LevelBufs L, NodeArrays nd, const int64_t *box_base, Box6 *boxes,
+                                                   const float4 *wpos, const float4 *wvel)
+{
+    const int k = blockIdx.x;
+    if (k >= L.K) return;
+    const int node = L.list[k], first = nd.first[node], n = nd.count[node];
+    const int nl = (int)ceil_div(n, BVH_LEAF);
+    Box6 *bx = boxes + box_base[k];
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+        Box6 b = box_empty();
+        const int e = min(n, (i + 1) * BVH_LEAF);
+        for (int m = i * BVH_LEAF; m < e; m++) box_add(b, wpos[first + m], wvel[first + m]);
+        bx[i] = b;
+    }
+    __syncthreads();
+    const int H = bvh_levels(nl);
+    int64_t off_prev = 0, off = nl;
+    for (int h = 1; h < H; h++) {
+        const int cnt = bvh_count(nl, h), cprev = bvh_count(nl, h - 1);
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            Box6 b = bx[off_prev + 2 * i];
+            if (2 * i + 1 < cprev) b = box_union(b, bx[off_prev + 2 * i + 1]);
+            bx[off + i] = b;
+        }
+        __syncthreads();
+        off_prev = off;
+        off += cnt;
+    }
+}
+
+__device__ __forceinline__ float point_box_d2(float4 p, float4 v, const Box6 &b, const Metric6 &m)
+{
+    float gx = fmaxf(0.f, fmaxf(b.plo.x - p.x, p.x - b.phi.x)), gy = fmaxf(0.f, fmaxf(b.plo.y - p.y, p.y - b.phi.y)),
+          gz = fmaxf(0.f, fmaxf(b.plo.z - p.z, p.z - b.phi.z));
+    float gu = fmaxf(0.f, fmaxf(b.vlo.x - v.x, v.x - b.vhi.x)), gv = fmaxf(0.f, fmaxf(b.vlo.y - v.y, v.y - b.vhi.y)),
+          gw = fmaxf(0.f, fmaxf(b.vlo.z - v.z, v.z - b.vhi.z));
+    return (gx * gx + gy * gy + gz * gz) * m.ax + (gu * gu + gv * gv + gw * gw) * m.av;
+}
+
+// Depth-first traversal of one node's hierarchy for one query.  mode 0:
+// nearest neighbour (radius shrinks to the best distance found); mode 1:
+// every candidate within the fixed radius (friends-of-friends at l).
+struct BvhView {
+    const Box6 *bx;
+    int nl, H;
+    int off[24];
+};
+
+__device__ __forceinline__ void bvh_view(BvhView &V, const Box6 *bx, int n)
+{
+    V.bx = bx;
+    V.nl = (int)ceil_div(n, BVH_LEAF);
+    V.H = bvh_levels(V.nl);
+    if (V.H > 24) V.H = 24;  // n <= 8 * 2^23 members per node (checked on the host)
+    int o = 0;
+    for (int h = 0; h < V.H && h < 24; h++) {
+        V.off[h] = o;
+        o += bvh_count(V.nl, h);
+    }
+}
+
+// ---- dense boxes at the linking length ----
+// A box whose float32 diameter under the node's metric is at most
+// l^2 (1 - 2^-17) holds only mutual friends (the float32 diameter is within
+// 8 ulps of the exact one), so all its members are joined once and a query
+// that reaches the whole box within the same margin joins it with a single
+// union.  These pairs lie strictly inside the linking length, never in the
+// tie band.  The flag is kept in the box's phi.w.
+#define RS_CLIQUE_MARGIN 0.99999237060546875  // 1 - 2^-17
+
+__device__ __forceinline__ float box_diam2(const Box6 &b, const Metric6 &m)
+{
+    float ex = b.phi.x - b.plo.x, ey = b.phi.y - b.plo.y, ez = b.phi.z - b.plo.z;
+    float eu = b.vhi.x - b.vlo.x, ev = b.vhi.y - b.vlo.y, ew = b.vhi.z - b.vlo.z;
+    return (ex * ex + ey * ey + ez * ez) * m.ax + (eu * eu + ev * ev + ew * ew) * m.av;
+}
+
+__device__ __forceinline__ float point_box_far2(float4 p, float4 v, const Box6 &b, const Metric6 &m)
+{
+    float fx = fmaxf(p.x - b.plo.x, b.phi.x - p.x), fy = fmaxf(p.y - b.plo.y, b.phi.y - p.y),
+          fz = fmaxf(p.z - b.plo.z, b.phi.z - p.z);
+    float fu = fmaxf(v.x - b.vlo.x, b.vhi.x - v.x), fv = fmaxf(v.y - b.vlo.y, b.vhi.y - v.y),
+          fw = fmaxf(v.z - b.vlo.z, b.vhi.z - v.z);
+    return (fx * fx + fy * fy + fz * fz) * m.ax + (fu * fu + fv * fv + fw * fw) * m.av;
+}
+
+// one block per node: flag the clique boxes, then join the members of every
+// maximal one (a clique box whose parent is not a clique)
+__global__ void __launch_bounds__(256) k_bvh_clique(LevelBufs L, NodeArrays nd, const int64_t *box_base, Box6 *boxes,
+                                                    int *parent, rs_dev_status *st)
+{
+    const int k = blockIdx.x;
+    if (k >= L.K) return;
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
     const Metric6 met = L.met[k];
-    const int q = q0 + threadIdx.x;
-    float4 pq = make_float4(0, 0, 0, 0), vq = pq;
-    if (q < n) {
-        pq = wpos[first + q];
-        vq = wvel[first + q];
+    const float lim = (float)(L.l2[k] * RS_CLIQUE_MARGIN);
+    BvhView V;
+    bvh_view(V, boxes + box_base[k], n);
+    Box6 *bx = boxes + box_base[k];
+    const int total = V.off[V.H - 1] + 1;
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+        const bool cl = box_diam2(bx[b], met) <= lim;
+        bx[b].phi.w = cl ? 1.f : 0.f;
     }
+    __syncthreads();
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+        if (bx[b].phi.w == 0.f) continue;
+        int h = 0;
+        while (h + 1 < V.H && V.off[h + 1] <= b) h++;
+        const int i = b - V.off[h];
+        if (h + 1 < V.H && bx[V.off[h + 1] + i / 2].phi.w != 0.f) continue;  // not maximal
+        const int m0 = i * (BVH_LEAF << h), m1 = min(n, (i + 1) * (BVH_LEAF << h));
+        for (int m = m0 + 1; m < m1; m++) uf_union(parent, first + m0, first + m, st);
+    }
+}
+
+// Warp-packet traversal: the 32 queries of one warp are consecutive members
+// in Morton order and walk the node's hierarchy together.  A box is opened
+// when it can matter to any lane (each lane tests it against its own query),
+// every box and leaf member is read once per warp (broadcast), and the shared
+// stack lives in shared memory.  Exact: a lane uses a box only through its
+// own point-to-box bound, which never excludes a member it needs.
+constexpr int PK_WARPS = 8;         // warps per block
+constexpr int PK_STACK = 64;        // stack entries per warp
+
+__device__ __forceinline__ void leaf_range(int i, int n, int &a, int &b)
+{
+    a = i * BVH_LEAF;
+    b = min(n, a + BVH_LEAF);
+}
+
+struct WarpJobs {
+    const int *rank;   // per warp job: node rank
+    const int *q0;     // first member of the warp's 32 queries
+    const int *out;    // where lane 0's result goes (lane l writes out + l)
+    int64_t count;
+};
+
+// nearest-neighbour distances, one warp per job of 32 consecutive members
+__global__ void __launch_bounds__(PK_WARPS * 32) k_bvh_nn(LevelBufs L, WarpJobs J, NodeArrays nd,
+                                                          const int64_t *box_base, const Box6 *boxes,
+                                                          const float4 *wpos, const float4 *wvel, const float *R2,
+                                                          float *out, rs_dev_status *st)
+{
+    __shared__ int stk_s[PK_WARPS][PK_STACK];
+    const int w = warp_id(), lane = lane_id();
+    const int64_t gw = (int64_t)blockIdx.x * PK_WARPS + w;
+    if (gw >= J.count) return;
+    const int k = J.rank[gw], q0 = J.q0[gw];
+    const int node = L.list[k], first = nd.first[node], n = nd.count[node];
+    if (q0 >= n) return;
+    const Metric6 met = L.met[k];
+    BvhView V;
+    bvh_view(V, boxes + box_base[k], n);
+    const int q = q0 + lane;
+    const bool valid = q < n;
+    const float4 pq = valid ? wpos[first + q] : make_float4(0, 0, 0, 0);
+    const float4 vq = valid ? wvel[first + q] : make_float4(0, 0, 0, 0);
+    // start from the node's radius when one is given (just above it, so a
+    // result at or above the start means "nothing within the radius")
+    const float start = R2 ? R2[k] * 1.00000095367431640625f : INFINITY;
+    float best = start;
+    // the leaves holding the warp's own members first (a tight starting bound)
+    const int e = min(n, q0 + 32);
+    const int own0 = q0 / BVH_LEAF, own1 = (e - 1) / BVH_LEAF;
+    {
+        const int a = own0 * BVH_LEAF, b = min(n, (own1 + 1) * BVH_LEAF);
+        for (int m = a; m < b; m++) {
+            const float4 pc = wpos[first + m], vc = wvel[first + m];
+            if (valid && m != q) best = fminf(best, d2_32(pq, vq, pc, vc, met));
+        }
+    }
+    int *stk = stk_s[w];
+    if (lane == 0) stk[0] = ((V.H - 1) << 24) | 0;
+    int sp = 1;
+    __syncwarp();
+    for (int it = 0; sp > 0 && it < (1 << 26); it++) {
+        const int ent = stk[--sp];
+        __syncwarp();
+        const int h = ent >> 24, i = ent & 0xffffff;
+        const Box6 bx = V.bx[V.off[h] + i];
+        const bool need = valid && point_box_d2(pq, vq, bx, met) <= best * RS_PRUNE_SLACK;
+        if (!__any_sync(0xffffffffu, need)) continue;
+        if (h == 0) {
+            if (i >= own0 && i <= own1) continue;
+            int a, b;
+            leaf_range(i, n, a, b);
+            for (int m = a; m < b; m++) {
+                const float4 pc = wpos[first + m], vc = wvel[first + m];
+                if (need) best = fminf(best, d2_32(pq, vq, pc, vc, met));
+            }
+            continue;
+        }
+        // children some lane can still use, the nearer (for the warp) visited first
+        const int cprev = bvh_count(V.nl, h - 1);
+        const int c0 = 2 * i, c1 = 2 * i + 1;
+        const Box6 b0 = V.bx[V.off[h - 1] + c0];
+        const float d0 = valid ? point_box_d2(pq, vq, b0, met) : INFINITY;
+        float d1 = INFINITY;
+        if (c1 < cprev) {
+            const Box6 b1 = V.bx[V.off[h - 1] + c1];
+            d1 = valid ? point_box_d2(pq, vq, b1, met) : INFINITY;
+        }
+        const float lim = best * RS_PRUNE_SLACK;
+        const bool u0 = __any_sync(0xffffffffu, d0 <= lim), u1 = __any_sync(0xffffffffu, d1 <= lim);
+        const float s0 = warp_sum(valid ? fminf(d0, 1e30f) : 0.f), s1 = warp_sum(valid ? fminf(d1, 1e30f) : 0.f);
+        const bool first0 = s0 <= s1;  // push the farther first
+        const int nc = (u0 ? 1 : 0) + (u1 ? 1 : 0);
+        if (sp + nc > PK_STACK) {
+            if (lane == 0) dev_fail(st, DEV_OVERFLOW, 54, node);
+            break;
+        }
+        if (lane == 0) {
+            int t = sp;
+            if (first0) {
+                if (u1) stk[t++] = ((h - 1) << 24) | c1;
+                if (u0) stk[t++] = ((h - 1) << 24) | c0;
+            } else {
+                if (u0) stk[t++] = ((h - 1) << 24) | c0;
+                if (u1) stk[t++] = ((h - 1) << 24) | c1;
+            }
+        }
+        sp += nc;
+        __syncwarp();
+    }
+    if (valid) out[J.out[gw] + lane] = best >= start ? INFINITY : best;
+}
+
+// nearest-neighbour distance of single sampled members (one thread each,
+// its own stack): the sample members are spread over the node, so they do not
+// share a traversal
+__global__ void __launch_bounds__(256) k_bvh_nn_sample(LevelBufs L, NodeArrays nd, const int64_t *box_base,
+                                                       const Box6 *boxes, const float4 *wpos, const float4 *wvel,
+                                                       const int64_t *soff, float *out, rs_dev_status *st)
+{
+    const int k = blockIdx.y;
+    const int node = L.list[k], first = nd.first[node], n = nd.count[node];
+    const int S = (int)(soff[k + 1] - soff[k]);
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int q = (int)(((int64_t)s * n) / S);
+    const Metric6 met = L.met[k];
+    BvhView V;
+    bvh_view(V, boxes + box_base[k], n);
+    const float4 pq = wpos[first + q], vq = wvel[first + q];
     float best = INFINITY;
-    for (int c0 = 0; c0 < n; c0 += TQ) {
-        __syncthreads();
-        if (c0 + threadIdx.x < n) {
-            cp[threadIdx.x] = wpos[first + c0 + threadIdx.x];
-            cv[threadIdx.x] = wvel[first + c0 + threadIdx.x];
+    int stk[BVH_STACK];
+    float slb[BVH_STACK];
+    int sp = 0;
+    stk[sp] = ((V.H - 1) << 24) | 0;
+    slb[sp++] = 0.f;
+    for (int it = 0; sp > 0 && it < (1 << 26); it++) {
+        sp--;
+        if (slb[sp] > best * RS_PRUNE_SLACK) continue;
+        const int e = stk[sp];
+        const int h = e >> 24, i = e & 0xffffff;
+        if (h == 0) {
+            int a, b;
+            leaf_range(i, n, a, b);
+            for (int m = a; m < b; m++)
+                if (m != q) best = fminf(best, d2_32(pq, vq, wpos[first + m], wvel[first + m], met));
+            continue;
         }
-        __syncthreads();
-        const int m = min(TQ, n - c0);
-        for (int j = 0; j < m; j++) {
-            if (c0 + j == q) continue;
-            best = fminf(best, d2_32(pq, vq, cp[j], cv[j], met));
+        const int cprev = bvh_count(V.nl, h - 1);
+        const int c0 = 2 * i, c1 = 2 * i + 1;
+        const float l0 = point_box_d2(pq, vq, V.bx[V.off[h - 1] + c0], met);
+        const float l1 = c1 < cprev ? point_box_d2(pq, vq, V.bx[V.off[h - 1] + c1], met) : INFINITY;
+        const bool n0 = l0 <= l1;
+        const int fa = n0 ? c1 : c0, ne = n0 ? c0 : c1;
+        const float lfa = n0 ? l1 : l0, lne = n0 ? l0 : l1;
+        const float lim = best * RS_PRUNE_SLACK;
+        if (sp + 2 > BVH_STACK) {
+            dev_fail(st, DEV_OVERFLOW, 57, node);
+            break;
+        }
+        if (lfa <= lim) {
+            stk[sp] = ((h - 1) << 24) | fa;
+            slb[sp++] = lfa;
+        }
+        if (lne <= lim) {
+            stk[sp] = ((h - 1) << 24) | ne;
+            slb[sp++] = lne;
         }
     }
-    if (q < n) dnn[first + q] = best;
+    out[soff[k] + s] = best;
+}
+
+// friends-of-friends at l, one warp per 32 consecutive members, pairs with
+// the candidate after the query in the node's member order
+__global__ void __launch_bounds__(PK_WARPS * 32) k_bvh_link(LevelBufs L, NodeArrays nd, const int64_t *box_base,
+                                                            const Box6 *boxes, const float4 *wpos,
+                                                            const float4 *wvel, const float *dnn, int *parent,
+                                                            rs_dev_status *st)
+{
+    __shared__ int stk_s[PK_WARPS][PK_STACK];
+    const int w = warp_id(), lane = lane_id();
+    const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x] + 32 * w;
+    const int node = L.list[k], first = nd.first[node], n = nd.count[node];
+    if (q0 >= n) return;
+    const Metric6 met = L.met[k];
+    const double l2 = L.l2[k], l = sqrt(l2);
+    const float lo = (float)(l2 * (1.0 - RS_BAND)), hi = (float)(l2 * (1.0 + RS_BAND));
+    const float tlo = (float)(l2 * (1.0 - 3e-6)), thi = (float)(l2 * (1.0 + 3e-6));
+    const float part = fmaxf(hi, thi);
+    const float lim = part * RS_PRUNE_SLACK;
+    const float cl_lim = (float)(l2 * RS_CLIQUE_MARGIN);
+    const int q = q0 + lane;
+    const bool active = q < n && dnn[first + q] <= part;
+    if (!__any_sync(0xffffffffu, active)) return;
+    BvhView V;
+    bvh_view(V, boxes + box_base[k], n);
+    const float4 pq = active ? wpos[first + q] : make_float4(0, 0, 0, 0);
+    const float4 vq = active ? wvel[first + q] : make_float4(0, 0, 0, 0);
+    int tie = 0;
+    int *stk = stk_s[w];
+    if (lane == 0) stk[0] = ((V.H - 1) << 24) | 0;
+    int sp = 1;
+    __syncwarp();
+    for (int it = 0; sp > 0 && it < (1 << 26); it++) {
+        const int ent = stk[--sp];
+        __syncwarp();
+        const int h = ent >> 24, i = ent & 0xffffff;
+        // boxes wholly before the warp's first query hold no candidate
+        if ((int64_t)(i + 1) * ((int64_t)BVH_LEAF << h) <= (int64_t)q0 + 1) continue;
+        const Box6 bx = V.bx[V.off[h] + i];
+        bool need = active && point_box_d2(pq, vq, bx, met) <= lim;
+        if (!__any_sync(0xffffffffu, need)) continue;
+        if (bx.phi.w != 0.f) {
+            // a clique box wholly within reach: one union with its first member
+            const bool covered = need && point_box_far2(pq, vq, bx, met) <= cl_lim;
+            if (covered) uf_union(parent, first + q, first + i * (BVH_LEAF << h), st);
+            need = need && !covered;
+            if (!__any_sync(0xffffffffu, need)) continue;
+        }
+        if (h == 0) {
+            int a, b;
+            leaf_range(i, n, a, b);
+            for (int m = max(a, q0 + 1); m < b; m++) {
+                const float dc = dnn[first + m];
+                if (dc > part) continue;
+                const float4 pc = wpos[first + m], vc = wvel[first + m];
+                if (!need || m <= q) continue;
+                const float d2 = d2_32(pq, vq, pc, vc, met);
+                if (d2 > part) continue;
+                bool link = d2 <= lo;
+                if (!link && (d2 <= hi || (d2 >= tlo && d2 <= thi))) {
+                    const double e64 = d2_64(pq, vq, pc, vc, met);
+                    link = e64 <= l2;
+                    if (l2 > 0 && e64 != l2 && fabs(sqrt(e64) - l) <= 1e-6 * l) tie++;
+                }
+                if (link) uf_union(parent, first + q, first + m, st);
+            }
+            continue;
+        }
+        const int cprev = bvh_count(V.nl, h - 1);
+        bool u[2] = {false, false};
+        for (int c = 0; c < 2; c++) {
+            const int ci = 2 * i + c;
+            if (ci >= cprev) break;
+            if ((int64_t)(ci + 1) * ((int64_t)BVH_LEAF << (h - 1)) <= (int64_t)q0 + 1) continue;
+            const Box6 cb = V.bx[V.off[h - 1] + ci];
+            u[c] = __any_sync(0xffffffffu, active && point_box_d2(pq, vq, cb, met) <= lim);
+        }
+        const int nc = (u[0] ? 1 : 0) + (u[1] ? 1 : 0);
+        if (sp + nc > PK_STACK) {
+            if (lane == 0) dev_fail(st, DEV_OVERFLOW, 55, node);
+            break;
+        }
+        if (lane == 0) {
+            int t = sp;
+            if (u[1]) stk[t++] = ((h - 1) << 24) | (2 * i + 1);
+            if (u[0]) stk[t++] = ((h - 1) << 24) | (2 * i);
+        }
+        sp += nc;
+        __syncwarp();
+    }
+    tie = warp_sum(tie);
+    if (lane == 0 && tie) atomicAdd(&L.tie[k], tie);
+}
+
+// ---- sampled bracket for the nearest-neighbour search ----
+// The exact nearest-neighbour distances of an evenly spread sample of a
+// node's members give a radius t_hi that lies above the node's f-quantile
+// with overwhelming probability (five binomial standard deviations).  The
+// search for every member then starts from t_hi instead of infinity: members
+// with a neighbour within t_hi get their exact float32 distance, the others
+// stop early with "none within t_hi".  Only values up to the k-th are needed
+// for the linking length; if the k-th value is not within t_hi the level
+// falls back to the unbounded search, so the result is always exact.
+constexpr int SMP_MAX = 2048;       // sample size per node (multiple of 32)
+
+__global__ void k_smp_prep(const int *list, int K, NodeArrays nd, int64_t *ns)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    ns[k] = min(nd.count[list[k]], SMP_MAX);
+}
+
+// full-search warp jobs: every 32 consecutive members of every node
+__global__ void k_full_jobs(const int *list, int K, NodeArrays nd, const int64_t *woff, int *jrank, int *jq0,
+                            int *jout)
+{
+    const int k = blockIdx.x;
+    if (k >= K) return;
+    const int node = list[k], first = nd.first[node];
+    const int64_t a = woff[k], c = woff[k + 1] - woff[k];
+    for (int64_t j = threadIdx.x; j < c; j += blockDim.x) {
+        jrank[a + j] = k;
+        jq0[a + j] = (int)(32 * j);
+        jout[a + j] = first + (int)(32 * j);
+    }
+}
+
+__global__ void k_full_prep(const int *list, int K, NodeArrays nd, int64_t *nw)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    nw[k] = ceil_div(nd.count[list[k]], 32);
+}
+
+// initial radius of the nearest-neighbour search: the sample's quantile at
+// f + 5 sigma (the exact f-quantile itself when the sample is the whole
+// node), widened by 16 band widths
+__global__ void k_smp_thresh(LevelBufs L, NodeArrays nd, const int64_t *soff, const float *sdnn, double f,
+                             float *R2)
+{
+    __shared__ float v[SMP_MAX];
+    const int k = blockIdx.x;
+    if (k >= L.K) return;
+    const int n = nd.count[L.list[k]];
+    const int64_t a = soff[k];
+    const int S = (int)(soff[k + 1] - a);
+    for (int i = threadIdx.x; i < SMP_MAX; i += blockDim.x) v[i] = i < S ? sdnn[a + i] : INFINITY;
+    __syncthreads();
+    for (int kk = 2; kk <= SMP_MAX; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < SMP_MAX / 2; t += blockDim.x) {
+                int i = 2 * j * (t / j) + (t % j), l = i + j;
+                bool up = (i & kk) == 0;
+                float x = v[i], y = v[l];
+                if ((x > y) == up) {
+                    v[i] = y;
+                    v[l] = x;
+                }
+            }
+            __syncthreads();
+        }
+    if (threadIdx.x == 0) {
+        double fq = f;
+        if (n > S) fq = fmin(1.0, f + 5.0 * sqrt(f * (1.0 - f) / (double)S));
+        long long idx = (long long)ceil(fq * (double)S) - 1;
+        if (idx < 0) idx = 0;
+        if (idx >= S) idx = S - 1;
+        const float t = v[idx];
+        R2[k] = isinf(t) ? INFINITY : (float)((double)t * (1.0 + 16.0 * RS_BAND));
+    }
+}
+
+// the level falls back to the full search when a node's k-th value is not
+// within its radius, or its linking length's band reaches past the radius
+__global__ void k_bracket_check(LevelBufs L, const float *R2, int *fallback)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.K) return;
+    // the whole float32 band around the k-th value must lie inside the radius,
+    // so no member that belongs in the band was cut off by it
+    const float t32 = __uint_as_float(L.sel_prefix[k]);
+    if (!((double)t32 * (1.0 + 4.0 * RS_BAND) <= (double)R2[k])) atomicExch(fallback, 1);
+}
+
+// ---- level-0 ordering along a 6D Morton curve (locality for the boxes) ----
+__device__ __forceinline__ unsigned long long morton6(const unsigned c[6])
+{
+    unsigned long long key = 0;
+    for (int bit = 6; bit >= 0; bit--)
+        for (int d = 0; d < 6; d++) key = (key << 1) | ((c[d] >> bit) & 1u);
+    return key;
+}
+
+__global__ void k_lvl_morton(LevelBufs L, NodeArrays nd, const float4 *wpos, const float4 *wvel,
+                             unsigned long long *keys, unsigned *vals)
+{
+    const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x];
+    const int node = L.list[k], first = nd.first[node], n = nd.count[node];
+    const int q = q0 + threadIdx.x;
+    if (q >= n) return;
+    const float4 pr = L.ref[2 * k], vr = L.ref[2 * k + 1];
+    const float ix = nd.sigx[node] > 0 ? (float)(1.0 / nd.sigx[node]) : 0.f;
+    const float iv = nd.sigv[node] > 0 ? (float)(1.0 / nd.sigv[node]) : 0.f;
+    const float4 p = wpos[first + q], v = wvel[first + q];
+    const float u[6] = {(p.x - pr.x) * ix, (p.y - pr.y) * ix, (p.z - pr.z) * ix,
+                        (v.x - vr.x) * iv, (v.y - vr.y) * iv, (v.z - vr.z) * iv};
+    unsigned c[6];
+    for (int d = 0; d < 6; d++) {
+        float t = (u[d] + 6.f) * (128.f / 12.f);
+        t = fminf(fmaxf(t, 0.f), 127.f);
+        c[d] = (unsigned)t;
+    }
+    const int64_t pidx = L.seg_off[k] + q;
+    keys[pidx] = ((unsigned long long)k << 42) | morton6(c);
+    vals[pidx] = (unsigned)(first + q);
 }
 
 // radix select: pass 0 digits bits 31..21, pass 1 bits 20..10, pass 2 bits 9..0
@@ -737,56 +1288,6 @@ __global__ void k_lvl_iota(LevelBufs L, NodeArrays nd, int *parent, int *csize, 
     cmin[first + q] = 0x7fffffff;
 }
 
-__global__ void __launch_bounds__(TQ) k_lvl_link(LevelBufs L, NodeArrays nd, const float4 *wpos,
-                                                 const float4 *wvel, const float *dnn, int *parent,
-                                                 rs_dev_status *st)
-{
-    __shared__ float4 cp[TQ], cv[TQ];
-    __shared__ float cd[TQ];
-    const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x];
-    const int node = L.list[k], first = nd.first[node], n = nd.count[node];
-    const Metric6 met = L.met[k];
-    const double l2 = L.l2[k], l = sqrt(l2);
-    const float lo = (float)(l2 * (1.0 - RS_BAND)), hi = (float)(l2 * (1.0 + RS_BAND));
-    const float tlo = (float)(l2 * (1.0 - 3e-6)), thi = (float)(l2 * (1.0 + 3e-6));
-    const float part = fmaxf(hi, thi);
-    const int q = q0 + threadIdx.x;
-    float4 pq = make_float4(0, 0, 0, 0), vq = pq;
-    bool active = false;
-    if (q < n) {
-        pq = wpos[first + q];
-        vq = wvel[first + q];
-        active = dnn[first + q] <= part;
-    }
-    int tie = 0;
-    for (int c0 = q0; c0 < n; c0 += TQ) {  // candidates c > q only
-        __syncthreads();
-        if (c0 + threadIdx.x < n) {
-            cp[threadIdx.x] = wpos[first + c0 + threadIdx.x];
-            cv[threadIdx.x] = wvel[first + c0 + threadIdx.x];
-            cd[threadIdx.x] = dnn[first + c0 + threadIdx.x];
-        }
-        __syncthreads();
-        if (!active) continue;
-        const int m = min(TQ, n - c0);
-        for (int j = 0; j < m; j++) {
-            const int c = c0 + j;
-            if (c <= q || cd[j] > part) continue;
-            const float d2 = d2_32(pq, vq, cp[j], cv[j], met);
-            if (d2 > part) continue;
-            bool link = d2 <= lo;
-            if (!link && (d2 <= hi || (d2 >= tlo && d2 <= thi))) {
-                const double e = d2_64(pq, vq, cp[j], cv[j], met);
-                link = e <= l2;
-                if (l2 > 0 && e != l2 && fabs(sqrt(e) - l) <= 1e-6 * l) tie++;
-            }
-            if (link) uf_union(parent, first + q, first + c, st);
-        }
-    }
-    tie = warp_sum(tie);
-    if (lane_id() == 0 && tie) atomicAdd(&L.tie[k], tie);
-}
-
 __global__ void k_lvl_comp(LevelBufs L, NodeArrays nd, const int *widx, int *parent, int *csize, int *cmin,
                            rs_dev_status *st)
 {
@@ -816,11 +1317,11 @@ __global__ void k_lvl_keys(LevelBufs L, NodeArrays nd, int *parent, const int *c
 
 __global__ void k_lvl_scatter(LevelBufs L, NodeArrays nd, int64_t LM, const unsigned long long *keys,
                               const unsigned *vals, const float4 *wpos, const float4 *wvel, const int *widx,
-                              float4 *wpos2, float4 *wvel2, int *widx2, unsigned *dest)
+                              float4 *wpos2, float4 *wvel2, int *widx2, unsigned *dest, int rank_shift)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= LM) return;
-    const int k = (int)(keys[p] >> 32);
+    const int k = (int)(keys[p] >> rank_shift);
     const int node = L.list[k];
     const int d = nd.first[node] + (int)(p - L.seg_off[k]);
     const unsigned s = vals[p];
@@ -1015,6 +1516,7 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
     int *cur = big_a, *nxt = big_b;
     int *cur_len = ctr + 0, *nxt_len = ctr + 1;
     int64_t sum_level = 0;
+    int n_fallback_levels = 0;
     for (int level = 0; level < 4096; level++) {
         int64_t K;
         RS_TRY(rs_read_i64(ctx, cur_len, 1, &K, "rs_refine6d"));
@@ -1065,42 +1567,125 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
 
         RS_LAUNCH(ctx, "rf_lvl_moments", k_lvl_moments, T, TQ, 0, L, nd, (const float4 *)wpos, (const float4 *)wvel);
         RS_LAUNCH(ctx, "rf_lvl_finalize", k_lvl_finalize, ceil_div(K, 128), 128, 0, L, nd, box);
-        RS_LAUNCH(ctx, "rf_lvl_nn", k_lvl_nn, T, TQ, 0, L, nd, (const float4 *)wpos, (const float4 *)wvel, dnn);
+        RS_WS(ctx, uint64_t, k0, WS_SORT_K0, LM);
+        RS_WS(ctx, uint64_t, k1, WS_SORT_K1, LM);
+        RS_WS(ctx, uint32_t, v0, WS_SORT_V0, LM);
+        RS_WS(ctx, uint32_t, v1, WS_SORT_V1, LM);
+        int rbits = 0;
+        while (rbits < 32 && ((uint64_t)(K - 1) >> rbits) != 0) rbits++;
+        if (level == 0) {
+            // order each big root's members along a 6D Morton curve; children
+            // keep this order through the stable child partition below
+            RS_LAUNCH(ctx, "rf_lvl_morton", k_lvl_morton, T, TQ, 0, L, nd, (const float4 *)wpos,
+                      (const float4 *)wvel, (unsigned long long *)k0, v0);
+            bool malt = false;
+            RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, LM, 42 + rbits, &malt));
+            const unsigned long long *mk = (const unsigned long long *)(malt ? k1 : k0);
+            const unsigned *mv = malt ? v1 : v0;
+            unsigned *mdest = (unsigned *)(malt ? v0 : v1);
+            RS_LAUNCH(ctx, "rf_lvl_scatter", k_lvl_scatter, ceil_div(LM, 256), 256, 0, L, nd, LM, mk, mv,
+                      (const float4 *)wpos, (const float4 *)wvel, (const int *)widx, wpos2, wvel2, widx2, mdest, 42);
+            RS_LAUNCH(ctx, "rf_lvl_copyback", k_lvl_copyback, ceil_div(LM, 256), 256, 0, LM, (const unsigned *)mdest,
+                      (const float4 *)wpos2, (const float4 *)wvel2, (const int *)widx2, wpos, wvel, widx);
+        }
+        // bounding-volume hierarchy of every big node
+        RS_WS(ctx, int64_t, bo, WS_RF_MISC3, (K + 1) + 8);
+        RS_LAUNCH(ctx, "rf_bvh_prep", k_bvh_prep, ceil_div(K, 256), 256, 0, (const int *)cur, (int)K, nd, bo);
+        RS_CUDA(ctx, cudaMemsetAsync(bo + K, 0, sizeof(int64_t), ctx->stream));
+        RS_TRY(rs_scan_i64(ctx, bo, K + 1, tot + 2));
+        int64_t NBX;
+        RS_TRY(rs_read_i64(ctx, tot + 2, 1, &NBX, "rs_refine6d"));
+        RS_WS(ctx, Box6, boxes, WS_RF_HIST, NBX);
+        RS_LAUNCH(ctx, "rf_bvh_build", k_bvh_build, K, 256, 0, L, nd, (const int64_t *)bo, boxes,
+                  (const float4 *)wpos, (const float4 *)wvel);
+        // ---- linking length: sampled bracket, bounded nearest neighbours, exact select ----
+        RS_WS(ctx, int64_t, ch, WS_RF_MISC4, 2 * (K + 1) + 8);
+        int64_t *nsm = ch, *stot = ch + (K + 1);
+        RS_LAUNCH(ctx, "rf_smp_prep", k_smp_prep, ceil_div(K, 256), 256, 0, (const int *)cur, (int)K, nd, nsm);
+        RS_CUDA(ctx, cudaMemsetAsync(nsm + K, 0, sizeof(int64_t), ctx->stream));
+        RS_TRY(rs_scan_i64(ctx, nsm, K + 1, stot));
+        int64_t SS;
+        RS_TRY(rs_read_i64(ctx, stot, 1, &SS, "rs_refine6d"));
+        RS_WS(ctx, float, sdnn, WS_RF_SDNN, SS + 32);
+        RS_WS(ctx, float, R2, WS_RF_R2, K + 8);
+        {
+            dim3 grid((unsigned)ceil_div(SMP_MAX, 256), (unsigned)K);
+            int pr = rs_prof_begin(ctx, "rf_smp_nn");
+            k_bvh_nn_sample<<<grid, 256, 0, ctx->stream>>>(L, nd, (const int64_t *)bo, (const Box6 *)boxes,
+                                                           (const float4 *)wpos, (const float4 *)wvel,
+                                                           (const int64_t *)nsm, sdnn, ctx->d_status);
+            ctx->launches++;
+            rs_prof_end(ctx, pr);
+            RS_CUDA(ctx, cudaGetLastError());
+        }
+        RS_LAUNCH(ctx, "rf_smp_thresh", k_smp_thresh, K, 256, 0, L, nd, (const int64_t *)nsm, (const float *)sdnn, f,
+                  R2);
+        int *fallback = ctr + 7;
+        RS_CUDA(ctx, cudaMemsetAsync(ctr + 7, 0, sizeof(int), ctx->stream));
+        // every member's nearest-neighbour distance, searched from the radius
+        RS_WS(ctx, int64_t, fw, WS_RF_MISC5, 2 * (K + 1) + 8);
+        int64_t *nw = fw, *wtot = fw + (K + 1);
+        RS_LAUNCH(ctx, "rf_full_prep", k_full_prep, ceil_div(K, 256), 256, 0, (const int *)cur, (int)K, nd, nw);
+        RS_CUDA(ctx, cudaMemsetAsync(nw + K, 0, sizeof(int64_t), ctx->stream));
+        RS_TRY(rs_scan_i64(ctx, nw, K + 1, wtot));
+        int64_t W;
+        RS_TRY(rs_read_i64(ctx, wtot, 1, &W, "rs_refine6d"));
+        RS_WS(ctx, int, jf, WS_RF_JOBS2, 3 * W + 8);
+        WarpJobs JF;
+        JF.rank = jf;
+        JF.q0 = jf + W;
+        JF.out = jf + 2 * W;
+        JF.count = W;
+        RS_LAUNCH(ctx, "rf_full_jobs", k_full_jobs, K, 128, 0, (const int *)cur, (int)K, nd, (const int64_t *)nw, jf,
+                  jf + W, jf + 2 * W);
+        RS_LAUNCH(ctx, "rf_lvl_nn", k_bvh_nn, ceil_div(W, PK_WARPS), PK_WARPS * 32, 0, L, JF, nd, (const int64_t *)bo,
+                  (const Box6 *)boxes, (const float4 *)wpos, (const float4 *)wvel, (const float *)R2, dnn,
+                  ctx->d_status);
         RS_LAUNCH(ctx, "rf_lvl_initk", k_lvl_initk, ceil_div(K, 128), 128, 0, L, nd, f);
         for (int pass = 0; pass < 3; pass++) {
             RS_LAUNCH(ctx, "rf_lvl_hist", k_lvl_hist, T, TQ, 0, L, nd, (const float *)dnn, pass);
             RS_LAUNCH(ctx, "rf_lvl_pick", k_lvl_pick, K, 32, 0, L, pass);
         }
+        RS_LAUNCH(ctx, "rf_bracket_check", k_bracket_check, ceil_div(K, 128), 128, 0, L, (const float *)R2, fallback);
+        int64_t fo;
+        RS_TRY(rs_read_i64(ctx, ctr + 6, 1, &fo, "rs_refine6d"));
+        if ((fo >> 32) != 0) {
+            // the bracket did not hold for some node: unbounded search
+            RS_LAUNCH(ctx, "rf_lvl_nn_full", k_bvh_nn, ceil_div(W, PK_WARPS), PK_WARPS * 32, 0, L, JF, nd,
+                      (const int64_t *)bo, (const Box6 *)boxes, (const float4 *)wpos, (const float4 *)wvel,
+                      (const float *)nullptr, dnn, ctx->d_status);
+            RS_LAUNCH(ctx, "rf_lvl_initk", k_lvl_initk, ceil_div(K, 128), 128, 0, L, nd, f);
+            for (int pass = 0; pass < 3; pass++) {
+                RS_LAUNCH(ctx, "rf_lvl_hist", k_lvl_hist, T, TQ, 0, L, nd, (const float *)dnn, pass);
+                RS_LAUNCH(ctx, "rf_lvl_pick", k_lvl_pick, K, 32, 0, L, pass);
+            }
+            n_fallback_levels++;
+        }
         RS_LAUNCH(ctx, "rf_lvl_band", k_lvl_band, T, TQ, 0, L, nd, (const float *)dnn);
         int64_t NB;
         RS_TRY(rs_read_i64(ctx, ctr + 4, 1, &NB, "rs_refine6d"));
-        NB &= 0xffffffffll;
-        RS_LAUNCH(ctx, "rf_lvl_band_exact", k_lvl_band_exact, NB, TQ, 0, L, nd, (const float4 *)wpos,
+        const int nbv = (int)(NB & 0xffffffffll);
+        RS_LAUNCH(ctx, "rf_lvl_band_exact", k_lvl_band_exact, nbv, TQ, 0, L, nd, (const float4 *)wpos,
                   (const float4 *)wvel, (const float *)dnn);
         RS_LAUNCH(ctx, "rf_lvl_l2", k_lvl_l2, K, 128, 0, L, nd, f, ctx->d_status);
         RS_LAUNCH(ctx, "rf_lvl_iota", k_lvl_iota, T, TQ, 0, L, nd, uf, csize, cmin);
-        RS_LAUNCH(ctx, "rf_lvl_link", k_lvl_link, T, TQ, 0, L, nd, (const float4 *)wpos, (const float4 *)wvel,
-                  (const float *)dnn, uf, ctx->d_status);
+        RS_LAUNCH(ctx, "rf_bvh_clique", k_bvh_clique, K, 256, 0, L, nd, (const int64_t *)bo, boxes, uf, ctx->d_status);
+        RS_LAUNCH(ctx, "rf_lvl_link", k_bvh_link, T, TQ, 0, L, nd, (const int64_t *)bo, (const Box6 *)boxes,
+                  (const float4 *)wpos, (const float4 *)wvel, (const float *)dnn, uf, ctx->d_status);
         RS_LAUNCH(ctx, "rf_lvl_comp", k_lvl_comp, T, TQ, 0, L, nd, (const int *)widx, uf, csize, cmin,
                   ctx->d_status);
         // reorder: children first, by smallest particle index, then the rest
-        RS_WS(ctx, uint64_t, k0, WS_SORT_K0, LM);
-        RS_WS(ctx, uint64_t, k1, WS_SORT_K1, LM);
-        RS_WS(ctx, uint32_t, v0, WS_SORT_V0, LM);
-        RS_WS(ctx, uint32_t, v1, WS_SORT_V1, LM);
         RS_LAUNCH(ctx, "rf_lvl_keys", k_lvl_keys, T, TQ, 0, L, nd, uf, (const int *)csize, (const int *)cmin,
                   (unsigned long long *)k0, v0, (int)min_n, ctx->d_status);
-        int kbits = 32;
-        while (kbits < 64 && ((uint64_t)(K - 1) >> (kbits - 32)) != 0) kbits++;
         bool alt = false;
-        RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, LM, kbits, &alt));
+        RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, LM, 32 + rbits, &alt));
         const unsigned long long *sk = (const unsigned long long *)(alt ? k1 : k0);
         const unsigned *sv = alt ? v1 : v0;
         unsigned *dest = (unsigned *)(alt ? v0 : v1);
         RS_LAUNCH(ctx, "rf_lvl_children", k_lvl_children, ceil_div(LM, 256), 256, 0, L, nd, LM, sk, sv, uf,
                   (const int *)csize, nxt, nxt_len, small_q, ctr + 2, ctx->d_status);
         RS_LAUNCH(ctx, "rf_lvl_scatter", k_lvl_scatter, ceil_div(LM, 256), 256, 0, L, nd, LM, sk, sv,
-                  (const float4 *)wpos, (const float4 *)wvel, (const int *)widx, wpos2, wvel2, widx2, dest);
+                  (const float4 *)wpos, (const float4 *)wvel, (const int *)widx, wpos2, wvel2, widx2, dest, 32);
         RS_LAUNCH(ctx, "rf_lvl_copyback", k_lvl_copyback, ceil_div(LM, 256), 256, 0, LM, (const unsigned *)dest,
                   (const float4 *)wpos2, (const float4 *)wvel2, (const int *)widx2, wpos, wvel, widx);
         RS_LAUNCH(ctx, "rf_lvl_tie", k_lvl_store_tie, ceil_div(K, 128), 128, 0, L, nd);
@@ -1137,7 +1722,8 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
     t->n_tieband = s4[1];
     t->n_levels = nn > 0 ? (int32_t)s4[2] + 1 : 0;
     t->sum_level_members = s4[3];
-    (void)sum_level;
+    t->sum_big_level_members = sum_level;
+    t->n_fallback_levels = n_fallback_levels;
     return RS_OK;
 }
 

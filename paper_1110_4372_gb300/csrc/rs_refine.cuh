@@ -19,6 +19,8 @@ struct rs_tree {
     int64_t n_members = 0;   // member slots
     int64_t n_nodes = 0, n_seeds = 0, n_tieband = 0, sum_level_members = 0;
     int32_t n_levels = 0;
+    int32_t n_fallback_levels = 0;  // big-node levels that needed the full nearest-neighbour search
+    int64_t sum_big_level_members = 0;
     double box = 0;
     NodeArrays nd{};
     int *members = nullptr;  // particle index per member slot
@@ -170,14 +172,21 @@ __device__ __forceinline__ void mom_atomic_add(MomAcc *g, const MomAcc &a)
     atomic_add128(&g->qv_lo, &g->qv_hi, a.qv_lo, a.qv_hi);
 }
 
-__device__ __forceinline__ double s128_to_double(unsigned long long lo, unsigned long long hi)
-{
-    return (double)(long long)hi * 18446744073709551616.0 + (double)lo;
-}
-
 __device__ __forceinline__ double u128_to_double(unsigned long long lo, unsigned long long hi)
 {
     return (double)hi * 18446744073709551616.0 + (double)lo;
+}
+
+// Signed 128-bit value to double: convert the magnitude (a small negative
+// value has a low word near 2^64, which would cancel against the high word).
+__device__ __forceinline__ double s128_to_double(unsigned long long lo, unsigned long long hi)
+{
+    if ((long long)hi < 0) {
+        unsigned long long nlo = ~lo + 1ull;
+        unsigned long long nhi = ~hi + (nlo == 0 ? 1ull : 0ull);
+        return -u128_to_double(nlo, nhi);
+    }
+    return u128_to_double(lo, hi);
 }
 
 struct MomOut {

@@ -37,7 +37,8 @@ class rs_params(C.Structure):
 class rs_stats(C.Structure):
     _fields_ = [("n_fof_groups", C.c_int64), ("n_members", C.c_int64), ("n_nodes", C.c_int64),
                 ("n_levels", C.c_int32), ("n_seeds", C.c_int64), ("n_halos", C.c_int64),
-                ("n_tieband6d", C.c_int64), ("sum_level_members", C.c_int64)]
+                ("n_tieband6d", C.c_int64), ("sum_level_members", C.c_int64),
+                ("sum_big_level_members", C.c_int64), ("n_fallback_levels", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -34,8 +34,11 @@ CONFIGS = {
     "c2": dict(n=2097152, box=40.0, n_halos=2500, nmin=20, nmax=200_000, sub_levels=1),
     "c3": dict(n=134217728, box=160.0, n_halos=150_000, nmin=20, nmax=1_000_000, sub_levels=2),
     "c5": dict(n=1073741824, box=320.0, n_halos=1_200_000, nmin=20, nmax=1_000_000, sub_levels=2),
+    # the 134M-particle workload at one eighth of its volume (same density,
+    # same mass function and hierarchy): a profiling-size case
+    "c3q": dict(n=16777216, box=80.0, n_halos=18_750, nmin=20, nmax=1_000_000, sub_levels=2),
 }
-CONFIG_INDEX = {"c1": 1, "c2": 2, "c3": 3, "c5": 5}
+CONFIG_INDEX = {"c1": 1, "c2": 2, "c3": 3, "c5": 5, "c3q": 6}
 
 DELTA_VIR = 360.0          # overdensity used for the generated halos' radii
 N_C_LEVELS = 256           # concentration drawn from 256 equally spaced values in [5, 15]
