@@ -107,6 +107,31 @@ rs_status rs_fof3d(rs_ctx *ctx, const float *pos, int32_t stride, int64_t n, dou
 rs_status rs_group_sort(rs_ctx *ctx, const int32_t *labels, int64_t n, int32_t min_n, int32_t *perm,
                         int64_t *offsets, int64_t offsets_cap, int64_t *n_groups, int64_t *n_members);
 
+/* rs_fof3d without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * when they need groups -- a plugin inside a host framework whose own pool
+ * allocator owns the device memory, a service that fixes its device memory
+ * budget at start-up, or a latency-critical loop that must not stall on an
+ * allocator or run out of memory mid-run.
+ *
+ * It writes the same labels as rs_fof3d (device pointers pos and labels,
+ * owned by the caller; work enqueued on cuda_stream, NULL = legacy default
+ * stream) and synchronises that stream before returning.  Every temporary
+ * lives in one fixed scratch array of about 9 MB inside the library image,
+ * which every GPU that loads the library holds until the process exits.
+ * Limits: at most 65536 particles, and a neighbour table of at most 2^20
+ * cells (about 7 linking lengths times 2^(20/3) per box side); beyond either,
+ * RS_ERR_TOO_LARGE and nothing runs.  Other errors as rs_fof3d (status code
+ * only; there is no context for a message).
+ *
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture on the device.  All calls share the one array
+ * and it keeps the last call's contents: calls that overlap on the GPU (from
+ * different streams or host threads) race on it and give wrong results. */
+rs_status rs_fof3d_static(const float *pos, int32_t stride, int64_t n, double box, double b, int32_t *labels,
+                          void *cuda_stream);
+
 /* ------------------------------------------------------------------------ */
 /* Phase-space hierarchy (Sec. 3.2, Eq. 1)                                   */
 /* ------------------------------------------------------------------------ */
