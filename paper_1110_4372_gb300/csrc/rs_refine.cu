@@ -778,7 +778,7 @@ struct WarpJobs {
 __global__ void __launch_bounds__(PK_WARPS * 32) k_bvh_nn(LevelBufs L, WarpJobs J, NodeArrays nd,
                                                           const int64_t *box_base, const Box6 *boxes,
                                                           const float4 *wpos, const float4 *wvel, const float *R2,
-                                                          float *out, rs_dev_status *st)
+                                                          const float *STOP, float *out, rs_dev_status *st)
 {
     __shared__ int stk_s[PK_WARPS][PK_STACK];
     const int w = warp_id(), lane = lane_id();
@@ -797,6 +797,9 @@ __global__ void __launch_bounds__(PK_WARPS * 32) k_bvh_nn(LevelBufs L, WarpJobs 
     // start from the node's radius when one is given (just above it, so a
     // result at or above the start means "nothing within the radius")
     const float start = R2 ? R2[k] * 1.00000095367431640625f : INFINITY;
+    // a lane whose best falls below the stop value is done: its member is
+    // certainly below the linking length and its exact value is not needed
+    const float stop = STOP ? STOP[k] : 0.f;
     float best = start;
     // the leaves holding the warp's own members first (a tight starting bound)
     const int e = min(n, q0 + 32);
@@ -817,7 +820,9 @@ __global__ void __launch_bounds__(PK_WARPS * 32) k_bvh_nn(LevelBufs L, WarpJobs 
         __syncwarp();
         const int h = ent >> 24, i = ent & 0xffffff;
         const Box6 bx = V.bx[V.off[h] + i];
-        const bool need = valid && point_box_d2(pq, vq, bx, met) <= best * RS_PRUNE_SLACK;
+        const bool live = valid && !(best < stop);
+        if (!__any_sync(0xffffffffu, live)) break;
+        const bool need = live && point_box_d2(pq, vq, bx, met) <= best * RS_PRUNE_SLACK;
         if (!__any_sync(0xffffffffu, need)) continue;
         if (h == 0) {
             if (i >= own0 && i <= own1) continue;
@@ -833,15 +838,15 @@ __global__ void __launch_bounds__(PK_WARPS * 32) k_bvh_nn(LevelBufs L, WarpJobs 
         const int cprev = bvh_count(V.nl, h - 1);
         const int c0 = 2 * i, c1 = 2 * i + 1;
         const Box6 b0 = V.bx[V.off[h - 1] + c0];
-        const float d0 = valid ? point_box_d2(pq, vq, b0, met) : INFINITY;
+        const float d0 = live ? point_box_d2(pq, vq, b0, met) : INFINITY;
         float d1 = INFINITY;
         if (c1 < cprev) {
             const Box6 b1 = V.bx[V.off[h - 1] + c1];
-            d1 = valid ? point_box_d2(pq, vq, b1, met) : INFINITY;
+            d1 = live ? point_box_d2(pq, vq, b1, met) : INFINITY;
         }
         const float lim = best * RS_PRUNE_SLACK;
         const bool u0 = __any_sync(0xffffffffu, d0 <= lim), u1 = __any_sync(0xffffffffu, d1 <= lim);
-        const float s0 = warp_sum(valid ? fminf(d0, 1e30f) : 0.f), s1 = warp_sum(valid ? fminf(d1, 1e30f) : 0.f);
+        const float s0 = warp_sum(live ? fminf(d0, 1e30f) : 0.f), s1 = warp_sum(live ? fminf(d1, 1e30f) : 0.f);
         const bool first0 = s0 <= s1;  // push the farther first
         const int nc = (u0 ? 1 : 0) + (u1 ? 1 : 0);
         if (sp + nc > PK_STACK) {
@@ -1025,13 +1030,15 @@ __global__ void __launch_bounds__(PK_WARPS * 32) k_bvh_link(LevelBufs L, NodeArr
 // stop early with "none within t_hi".  Only values up to the k-th are needed
 // for the linking length; if the k-th value is not within t_hi the level
 // falls back to the unbounded search, so the result is always exact.
-constexpr int SMP_MAX = 2048;       // sample size per node (multiple of 32)
+constexpr int SMP_MAX = 1024;       // sample size per node
+constexpr int SMP_MIN_NODE = 4096;  // smaller nodes are searched without a bracket
 
 __global__ void k_smp_prep(const int *list, int K, NodeArrays nd, int64_t *ns)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
-    ns[k] = min(nd.count[list[k]], SMP_MAX);
+    const int n = nd.count[list[k]];
+    ns[k] = n > SMP_MIN_NODE ? SMP_MAX : 0;
 }
 
 // full-search warp jobs: every 32 consecutive members of every node
@@ -1056,11 +1063,12 @@ __global__ void k_full_prep(const int *list, int K, NodeArrays nd, int64_t *nw)
     nw[k] = ceil_div(nd.count[list[k]], 32);
 }
 
-// initial radius of the nearest-neighbour search: the sample's quantile at
-// f + 5 sigma (the exact f-quantile itself when the sample is the whole
-// node), widened by 16 band widths
+// bracket of the search from the sample: the radius R2 is the sample's
+// quantile at f + 5 sigma widened by 16 band widths; the stop value is the
+// quantile at f - 5 sigma narrowed by 16 band widths (a member with a
+// neighbour closer than it is certainly below the linking length)
 __global__ void k_smp_thresh(LevelBufs L, NodeArrays nd, const int64_t *soff, const float *sdnn, double f,
-                             float *R2)
+                             float *R2, float *STOP)
 {
     __shared__ float v[SMP_MAX];
     const int k = blockIdx.x;
@@ -1084,19 +1092,24 @@ __global__ void k_smp_thresh(LevelBufs L, NodeArrays nd, const int64_t *soff, co
             __syncthreads();
         }
     if (threadIdx.x == 0) {
-        double fq = f;
-        if (n > S) fq = fmin(1.0, f + 5.0 * sqrt(f * (1.0 - f) / (double)S));
-        long long idx = (long long)ceil(fq * (double)S) - 1;
-        if (idx < 0) idx = 0;
-        if (idx >= S) idx = S - 1;
-        const float t = v[idx];
-        R2[k] = isinf(t) ? INFINITY : (float)((double)t * (1.0 + 16.0 * RS_BAND));
+        if (S == 0) {  // not sampled: unbounded search, no early stop
+            R2[k] = INFINITY;
+            STOP[k] = 0.f;
+        } else {
+            const double sd = 5.0 * sqrt(f * (1.0 - f) / (double)S);
+            long long hi = (long long)ceil(fmin(1.0, f + sd) * (double)S) - 1;
+            long long lo = (long long)ceil(fmax(0.0, f - sd) * (double)S) - 2;
+            hi = hi < 0 ? 0 : (hi >= S ? S - 1 : hi);
+            const float th = v[hi];
+            R2[k] = isinf(th) ? INFINITY : (float)((double)th * (1.0 + 16.0 * RS_BAND));
+            STOP[k] = lo < 0 ? 0.f : (float)((double)v[lo] * (1.0 - 16.0 * RS_BAND));
+        }
     }
 }
 
-// the level falls back to the full search when a node's k-th value is not
-// within its radius, or its linking length's band reaches past the radius
-__global__ void k_bracket_check(LevelBufs L, const float *R2, int *fallback)
+// the level falls back to the full search when the float32 band around a
+// node's k-th value is not inside (stop, radius)
+__global__ void k_bracket_check(LevelBufs L, const float *R2, const float *STOP, int *fallback)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= L.K) return;
@@ -1104,6 +1117,7 @@ __global__ void k_bracket_check(LevelBufs L, const float *R2, int *fallback)
     // so no member that belongs in the band was cut off by it
     const float t32 = __uint_as_float(L.sel_prefix[k]);
     if (!((double)t32 * (1.0 + 4.0 * RS_BAND) <= (double)R2[k])) atomicExch(fallback, 1);
+    if (!((double)t32 * (1.0 - 4.0 * RS_BAND) >= (double)STOP[k])) atomicExch(fallback, 1);
 }
 
 // ---- level-0 ordering along a 6D Morton curve (locality for the boxes) ----
@@ -1607,8 +1621,9 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         int64_t SS;
         RS_TRY(rs_read_i64(ctx, stot, 1, &SS, "rs_refine6d"));
         RS_WS(ctx, float, sdnn, WS_RF_SDNN, SS + 32);
-        RS_WS(ctx, float, R2, WS_RF_R2, K + 8);
-        {
+        RS_WS(ctx, float, R2, WS_RF_R2, 2 * K + 8);
+        float *STOP = R2 + K;
+        if (SS > 0) {
             dim3 grid((unsigned)ceil_div(SMP_MAX, 256), (unsigned)K);
             int pr = rs_prof_begin(ctx, "rf_smp_nn");
             k_bvh_nn_sample<<<grid, 256, 0, ctx->stream>>>(L, nd, (const int64_t *)bo, (const Box6 *)boxes,
@@ -1619,7 +1634,7 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
             RS_CUDA(ctx, cudaGetLastError());
         }
         RS_LAUNCH(ctx, "rf_smp_thresh", k_smp_thresh, K, 256, 0, L, nd, (const int64_t *)nsm, (const float *)sdnn, f,
-                  R2);
+                  R2, STOP);
         int *fallback = ctr + 7;
         RS_CUDA(ctx, cudaMemsetAsync(ctr + 7, 0, sizeof(int), ctx->stream));
         // every member's nearest-neighbour distance, searched from the radius
@@ -1639,21 +1654,22 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         RS_LAUNCH(ctx, "rf_full_jobs", k_full_jobs, K, 128, 0, (const int *)cur, (int)K, nd, (const int64_t *)nw, jf,
                   jf + W, jf + 2 * W);
         RS_LAUNCH(ctx, "rf_lvl_nn", k_bvh_nn, ceil_div(W, PK_WARPS), PK_WARPS * 32, 0, L, JF, nd, (const int64_t *)bo,
-                  (const Box6 *)boxes, (const float4 *)wpos, (const float4 *)wvel, (const float *)R2, dnn,
-                  ctx->d_status);
+                  (const Box6 *)boxes, (const float4 *)wpos, (const float4 *)wvel, (const float *)R2,
+                  (const float *)STOP, dnn, ctx->d_status);
         RS_LAUNCH(ctx, "rf_lvl_initk", k_lvl_initk, ceil_div(K, 128), 128, 0, L, nd, f);
         for (int pass = 0; pass < 3; pass++) {
             RS_LAUNCH(ctx, "rf_lvl_hist", k_lvl_hist, T, TQ, 0, L, nd, (const float *)dnn, pass);
             RS_LAUNCH(ctx, "rf_lvl_pick", k_lvl_pick, K, 32, 0, L, pass);
         }
-        RS_LAUNCH(ctx, "rf_bracket_check", k_bracket_check, ceil_div(K, 128), 128, 0, L, (const float *)R2, fallback);
+        RS_LAUNCH(ctx, "rf_bracket_check", k_bracket_check, ceil_div(K, 128), 128, 0, L, (const float *)R2,
+                  (const float *)STOP, fallback);
         int64_t fo;
         RS_TRY(rs_read_i64(ctx, ctr + 6, 1, &fo, "rs_refine6d"));
         if ((fo >> 32) != 0) {
             // the bracket did not hold for some node: unbounded search
             RS_LAUNCH(ctx, "rf_lvl_nn_full", k_bvh_nn, ceil_div(W, PK_WARPS), PK_WARPS * 32, 0, L, JF, nd,
                       (const int64_t *)bo, (const Box6 *)boxes, (const float4 *)wpos, (const float4 *)wvel,
-                      (const float *)nullptr, dnn, ctx->d_status);
+                      (const float *)nullptr, (const float *)nullptr, dnn, ctx->d_status);
             RS_LAUNCH(ctx, "rf_lvl_initk", k_lvl_initk, ceil_div(K, 128), 128, 0, L, nd, f);
             for (int pass = 0; pass < 3; pass++) {
                 RS_LAUNCH(ctx, "rf_lvl_hist", k_lvl_hist, T, TQ, 0, L, nd, (const float *)dnn, pass);
