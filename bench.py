@@ -167,6 +167,43 @@ def reference_arm(args, cat, cfg_json):
     print(json.dumps(line), flush=True)
 
 
+# ---- replicas on N GPUs (one process per GPU, launched by torchrun) ----
+def replica_env():
+    """(world size, rank, local rank) from the torchrun environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def init_replicas(world: int, local: int, backend: str = "nccl"):
+    """Process group for the barrier and the max-over-ranks timing; None for
+    a single process.  Replicas exchange nothing else: each runs the whole
+    workload on its own GPU."""
+    if world <= 1:
+        return None
+    import torch
+    import torch.distributed as dist
+    if backend == "nccl":
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist.init_process_group(backend)
+    return dist
+
+
+def max_over_ranks(x: float, dist, device: str = "cuda") -> float:
+    """The largest value of x over all ranks (x itself without a group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, seconds: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -180,9 +217,7 @@ def main():
     ap.add_argument("--ref-side", type=float, default=1.0 / 8.0, help="sub-cube side per reference step")
     args = ap.parse_args()
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = replica_env()
 
     cfg = synth.CONFIGS[args.config]
     cfg_json = {"workload": WORKLOADS[args.config], "name": args.config, "particles": cfg["n"], "box": cfg["box"],
@@ -200,10 +235,7 @@ def main():
     from paper_1110_4372_gb300 import rsgpu
 
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dist = init_replicas(world, local)
 
     cat = synth.generate(args.config)
     n = cat.n
@@ -241,11 +273,8 @@ def main():
     ms = ev0.elapsed_time(ev1) / args.steps
     prof = rsgpu.rs_profile_read(ctx)
     launches = rsgpu.rs_launch_count(ctx) // max(args.steps, 1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n / (ms * 1e-3)
+    ms = max_over_ranks(ms, dist)
+    value = whole_job_rate(n, world, ms * 1e-3)
 
     # ---- end to end through the C ABI with pinned host buffers ----
     e2e = None
@@ -262,12 +291,8 @@ def main():
         for _ in range(k):
             rsgpu.rs_find_halos(ctx, hp, hv, cat.box, p, halo_id=hout)
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / k
-        if dist:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * n / dt, "unit": "particles/s", "h2d_bytes_per_step": 2 * 12 * n,
+        dt = max_over_ranks((time.perf_counter() - t0) / k, dist)
+        e2e = {"value": whole_job_rate(n, world, dt), "unit": "particles/s", "h2d_bytes_per_step": 2 * 12 * n,
                "d2h_bytes_per_step": 4 * n, "ms_per_step": 1e3 * dt}
 
     if rank != 0:
