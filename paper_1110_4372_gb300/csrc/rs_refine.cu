@@ -561,7 +561,7 @@ __global__ void k_lvl_finalize(LevelBufs L, NodeArrays nd, double box)
     L.met[k] = metric_of(o.sigx, o.sigv);
 }
 
-// ---- buckets of 32 members, super-buckets of 32 buckets, raw-coordinate boxes ----
+// ---- raw-coordinate boxes ----
 // A box is (lo, hi) over the six raw float32 coordinates of its members (the
 // unwrapped positions and the velocities).  The gap between two boxes along
 // an axis is one float32 subtraction of exact input values, so the box
@@ -576,30 +576,106 @@ struct Box6 {
     float4 plo, phi, vlo, vhi;
 };
 
-// ---- per-node bounding-volume hierarchy over the member range ----
-// Leaves hold BVH_LEAF consecutive members (the range is in 6D Morton order);
-// box (h, i) of level h covers leaves [i 2^h, (i+1) 2^h) and is the union of
-// boxes (h-1, 2i) and (h-1, 2i+1).  Boxes of a node are stored level by
-// level starting at its base offset.
-constexpr int BVH_LEAF = 32;
-constexpr int BVH_STACK = 40;
+// Boxes of one level's hierarchies as three float4 streams (the lows and
+// highs of the six coordinates, 48 bytes a box) and one flag byte, so a warp
+// reading 32 consecutive boxes uses every byte of every sector it touches.
+struct BoxStore {
+    float4 *a;         // plo.x, plo.y, plo.z, vlo.x
+    float4 *b;         // vlo.y, vlo.z, phi.x, phi.y
+    float4 *c;         // phi.z, vhi.x, vhi.y, vhi.z
+    unsigned char *cl; // clique flag
+};
 
-__device__ __forceinline__ int bvh_count(int nl, int h) { return (nl + (1 << h) - 1) >> h; }
+__device__ __forceinline__ Box6 box_get(const BoxStore &S, int64_t i)
+{
+    const float4 x = S.a[i], y = S.b[i], z = S.c[i];
+    Box6 r;
+    r.plo = make_float4(x.x, x.y, x.z, 0.f);
+    r.vlo = make_float4(x.w, y.x, y.y, 0.f);
+    r.phi = make_float4(y.z, y.w, z.x, 0.f);
+    r.vhi = make_float4(z.y, z.z, z.w, 0.f);
+    return r;
+}
+
+__device__ __forceinline__ void box_put(const BoxStore &S, int64_t i, const Box6 &r)
+{
+    S.a[i] = make_float4(r.plo.x, r.plo.y, r.plo.z, r.vlo.x);
+    S.b[i] = make_float4(r.vlo.y, r.vlo.z, r.phi.x, r.phi.y);
+    S.c[i] = make_float4(r.phi.z, r.vhi.x, r.vhi.y, r.vhi.z);
+}
+
+__device__ __forceinline__ BoxStore box_shift(const BoxStore &S, int64_t base)
+{
+    BoxStore r;
+    r.a = S.a + base;
+    r.b = S.b + base;
+    r.c = S.c + base;
+    r.cl = S.cl + base;
+    return r;
+}
+
+// The searched members of one level, packed to the six coordinates (24
+// bytes a member, by slot): written while the hierarchy is built.
+struct MemberStore {
+    float4 *a;  // px, py, pz, vx
+    float2 *b;  // vy, vz
+};
+
+__device__ __forceinline__ void mem_get(const MemberStore &M, int64_t i, float4 &p, float4 &v)
+{
+    const float4 x = M.a[i];
+    const float2 y = M.b[i];
+    p = make_float4(x.x, x.y, x.z, 0.f);
+    v = make_float4(x.w, y.x, y.y, 0.f);
+}
+
+__device__ __forceinline__ MemberStore mem_shift(const MemberStore &M, int64_t base)
+{
+    MemberStore r;
+    r.a = M.a + base;
+    r.b = M.b + base;
+    return r;
+}
+
+// ---- per-node 32-ary bounding-volume hierarchy over the member range ----
+// Leaves hold BVH_LEAF = 32 consecutive members (the range is in 6D Morton
+// order); box (h, i) of level h is the union of boxes (h-1, 32i .. 32i+31),
+// so it spans members [i 32^(h+1), (i+1) 32^(h+1)).  The fan-out equals the
+// warp width: a search gives each lane one child box of the box it opens, or
+// one member of the leaf it scans.  Boxes of a node are stored level by
+// level from its base offset.
+constexpr int BVH_LEAF = 32;
+constexpr int BVH_LOG = 5;  // log2 of the leaf size and of the fan-out
+constexpr int BVH_MAXH = 8;
+
+__device__ __forceinline__ int bvh_count(int nl, int h)
+{
+    for (int j = 0; j < h; j++) nl = (nl + 31) >> BVH_LOG;
+    return nl;
+}
 
 __device__ __forceinline__ int bvh_levels(int nl)
 {
-    int h = 0;
-    while (bvh_count(nl, h) > 1) h++;
-    return h + 1;
+    int h = 1;
+    while (nl > 1) {
+        nl = (nl + 31) >> BVH_LOG;
+        h++;
+    }
+    return h;
 }
 
 __device__ __forceinline__ int64_t bvh_total(int nl)
 {
-    int64_t t = 0;
-    const int H = bvh_levels(nl);
-    for (int h = 0; h < H; h++) t += bvh_count(nl, h);
+    int64_t t = nl;
+    while (nl > 1) {
+        nl = (nl + 31) >> BVH_LOG;
+        t += nl;
+    }
     return t;
 }
+
+// first member of box (h, i) and the end of its member range
+__device__ __forceinline__ int64_t bvh_m0(int h, int i) { return (int64_t)i << (BVH_LOG * (h + 1)); }
 
 __global__ void k_bvh_prep(const int *list, int K, NodeArrays nd, int64_t *nbox)
 {
@@ -625,44 +701,50 @@ __device__ __forceinline__ void box_add(Box6 &b, float4 p, float4 v)
     b.vhi.x = fmaxf(b.vhi.x, v.x); b.vhi.y = fmaxf(b.vhi.y, v.y); b.vhi.z = fmaxf(b.vhi.z, v.z);
 }
 
-__device__ __forceinline__ Box6 box_union(const Box6 &a, const Box6 &c)
+__device__ __forceinline__ void box_merge(Box6 &b, const Box6 &c)
 {
-    Box6 b;
-    b.plo = make_float4(fminf(a.plo.x, c.plo.x), fminf(a.plo.y, c.plo.y), fminf(a.plo.z, c.plo.z), 0.f);
-    b.phi = make_float4(fmaxf(a.phi.x, c.phi.x), fmaxf(a.phi.y, c.phi.y), fmaxf(a.phi.z, c.phi.z), 0.f);
-    b.vlo = make_float4(fminf(a.vlo.x, c.vlo.x), fminf(a.vlo.y, c.vlo.y), fminf(a.vlo.z, c.vlo.z), 0.f);
-    b.vhi = make_float4(fmaxf(a.vhi.x, c.vhi.x), fmaxf(a.vhi.y, c.vhi.y), fmaxf(a.vhi.z, c.vhi.z), 0.f);
-    return b;
+    b.plo.x = fminf(b.plo.x, c.plo.x); b.plo.y = fminf(b.plo.y, c.plo.y); b.plo.z = fminf(b.plo.z, c.plo.z);
+    b.phi.x = fmaxf(b.phi.x, c.phi.x); b.phi.y = fmaxf(b.phi.y, c.phi.y); b.phi.z = fmaxf(b.phi.z, c.phi.z);
+    b.vlo.x = fminf(b.vlo.x, c.vlo.x); b.vlo.y = fminf(b.vlo.y, c.vlo.y); b.vlo.z = fminf(b.vlo.z, c.vlo.z);
+    b.vhi.x = fmaxf(b.vhi.x, c.vhi.x); b.vhi.y = fmaxf(b.vhi.y, c.vhi.y); b.vhi.z = fmaxf(b.vhi.z, c.vhi.z);
 }
 
 // one block builds one node's hierarchy, level by level
-__global__ void __launch_bounds__(256) k_bvh_build(LevelBufs L, NodeArrays nd, const int64_t *box_base, Box6 *boxes,
-                                                   const float4 *wpos, const float4 *wvel)
+__global__ void __launch_bounds__(256) k_bvh_build(LevelBufs L, NodeArrays nd, const int64_t *box_base,
+                                                   BoxStore B, MemberStore MS, const float4 *wpos, const float4 *wvel)
 {
     const int k = blockIdx.x;
     if (k >= L.K) return;
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
     const int nl = (int)ceil_div(n, BVH_LEAF);
-    Box6 *bx = boxes + box_base[k];
+    const BoxStore bx = box_shift(B, box_base[k]);
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+        const float4 p = wpos[first + m], v = wvel[first + m];
+        MS.a[first + m] = make_float4(p.x, p.y, p.z, v.x);
+        MS.b[first + m] = make_float2(v.y, v.z);
+    }
     for (int i = threadIdx.x; i < nl; i += blockDim.x) {
         Box6 b = box_empty();
         const int e = min(n, (i + 1) * BVH_LEAF);
         for (int m = i * BVH_LEAF; m < e; m++) box_add(b, wpos[first + m], wvel[first + m]);
-        bx[i] = b;
+        box_put(bx, i, b);
     }
     __syncthreads();
     const int H = bvh_levels(nl);
     int64_t off_prev = 0, off = nl;
+    int cprev = nl;
     for (int h = 1; h < H; h++) {
-        const int cnt = bvh_count(nl, h), cprev = bvh_count(nl, h - 1);
+        const int cnt = (cprev + 31) >> BVH_LOG;
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-            Box6 b = bx[off_prev + 2 * i];
-            if (2 * i + 1 < cprev) b = box_union(b, bx[off_prev + 2 * i + 1]);
-            bx[off + i] = b;
+            Box6 b = box_get(bx, off_prev + 32 * i);
+            const int e = min(cprev, 32 * i + 32);
+            for (int c = 32 * i + 1; c < e; c++) box_merge(b, box_get(bx, off_prev + c));
+            box_put(bx, off + i, b);
         }
         __syncthreads();
         off_prev = off;
         off += cnt;
+        cprev = cnt;
     }
 }
 
@@ -675,25 +757,24 @@ __device__ __forceinline__ float point_box_d2(float4 p, float4 v, const Box6 &b,
     return (gx * gx + gy * gy + gz * gz) * m.ax + (gu * gu + gv * gv + gw * gw) * m.av;
 }
 
-// Depth-first traversal of one node's hierarchy for one query.  mode 0:
-// nearest neighbour (radius shrinks to the best distance found); mode 1:
-// every candidate within the fixed radius (friends-of-friends at l).
 struct BvhView {
-    const Box6 *bx;
+    BoxStore S;
     int nl, H;
-    int off[24];
+    int off[BVH_MAXH];
+    int cnt[BVH_MAXH];
 };
 
-__device__ __forceinline__ void bvh_view(BvhView &V, const Box6 *bx, int n)
+__device__ __forceinline__ void bvh_view(BvhView &V, const BoxStore &B, int64_t base, int n)
 {
-    V.bx = bx;
+    V.S = box_shift(B, base);
     V.nl = (int)ceil_div(n, BVH_LEAF);
-    V.H = bvh_levels(V.nl);
-    if (V.H > 24) V.H = 24;  // n <= 8 * 2^23 members per node (checked on the host)
-    int o = 0;
-    for (int h = 0; h < V.H && h < 24; h++) {
+    V.H = min(bvh_levels(V.nl), BVH_MAXH);  // n <= 2^26 members per node (checked on the host): H <= 6
+    int o = 0, c = V.nl;
+    for (int h = 0; h < BVH_MAXH; h++) {
         V.off[h] = o;
-        o += bvh_count(V.nl, h);
+        V.cnt[h] = c;
+        o += c;
+        c = (c + 31) >> BVH_LOG;
     }
 }
 
@@ -724,7 +805,7 @@ __device__ __forceinline__ float point_box_far2(float4 p, float4 v, const Box6 &
 
 // one block per node: flag the clique boxes, then join the members of every
 // maximal one (a clique box whose parent is not a clique)
-__global__ void __launch_bounds__(256) k_bvh_clique(LevelBufs L, NodeArrays nd, const int64_t *box_base, Box6 *boxes,
+__global__ void __launch_bounds__(256) k_bvh_clique(LevelBufs L, NodeArrays nd, const int64_t *box_base, BoxStore B,
                                                     int *parent, rs_dev_status *st)
 {
     const int k = blockIdx.x;
@@ -733,289 +814,419 @@ __global__ void __launch_bounds__(256) k_bvh_clique(LevelBufs L, NodeArrays nd, 
     const Metric6 met = L.met[k];
     const float lim = (float)(L.l2[k] * RS_CLIQUE_MARGIN);
     BvhView V;
-    bvh_view(V, boxes + box_base[k], n);
-    Box6 *bx = boxes + box_base[k];
+    bvh_view(V, B, box_base[k], n);
     const int total = V.off[V.H - 1] + 1;
-    for (int b = threadIdx.x; b < total; b += blockDim.x) {
-        const bool cl = box_diam2(bx[b], met) <= lim;
-        bx[b].phi.w = cl ? 1.f : 0.f;
-    }
+    for (int b = threadIdx.x; b < total; b += blockDim.x) V.S.cl[b] = box_diam2(box_get(V.S, b), met) <= lim ? 1 : 0;
     __syncthreads();
     for (int b = threadIdx.x; b < total; b += blockDim.x) {
-        if (bx[b].phi.w == 0.f) continue;
+        if (!V.S.cl[b]) continue;
         int h = 0;
         while (h + 1 < V.H && V.off[h + 1] <= b) h++;
         const int i = b - V.off[h];
-        if (h + 1 < V.H && bx[V.off[h + 1] + i / 2].phi.w != 0.f) continue;  // not maximal
-        const int m0 = i * (BVH_LEAF << h), m1 = min(n, (i + 1) * (BVH_LEAF << h));
+        if (h + 1 < V.H && V.S.cl[V.off[h + 1] + (i >> BVH_LOG)]) continue;  // not maximal
+        const int m0 = (int)bvh_m0(h, i), m1 = (int)min((int64_t)n, bvh_m0(h, i + 1));
         for (int m = m0 + 1; m < m1; m++) uf_union(parent, first + m0, first + m, st);
     }
 }
 
-// Warp-packet traversal: the 32 queries of one warp are consecutive members
-// in Morton order and walk the node's hierarchy together.  A box is opened
-// when it can matter to any lane (each lane tests it against its own query),
-// every box and leaf member is read once per warp (broadcast), and the shared
-// stack lives in shared memory.  Exact: a lane uses a box only through its
-// own point-to-box bound, which never excludes a member it needs.
-constexpr int PK_WARPS = 8;         // warps per block
-constexpr int PK_STACK = 64;        // stack entries per warp
+// ---- warp-per-query search over the 32-ary hierarchy ----
+// One query at a time per warp.  Opening a box, lane c bounds the query's
+// distance to child box c (a float32 point-to-box gap, within 8 ulps of the
+// exact one; a box is skipped only when the bound exceeds the radius by
+// 2^-18, so no member that could change a float32 result is skipped).
+// Scanning a leaf, lane c evaluates member c and the warp minimum (redux on
+// the bit patterns, which order like the non-negative floats) updates the
+// radius.  The leaves under an opened box are scanned nearest first and
+// re-tested as the radius shrinks; needed inner boxes are pushed on a
+// shared-memory stack farthest first, each with its bound.
+constexpr int W_WARPS = 8;    // warps per block of the search kernels
+constexpr int W_STACK = 192;  // stack entries per warp: at most 31 pending per level
+constexpr unsigned FULLW = 0xffffffffu;
 
-__device__ __forceinline__ void leaf_range(int i, int n, int &a, int &b)
+__device__ __forceinline__ unsigned ford(float x) { return __float_as_uint(x); }
+
+__device__ __forceinline__ float wmin(float x) { return __uint_as_float(__reduce_min_sync(FULLW, ford(x))); }
+
+__device__ __forceinline__ float4 shfl4(float4 a, int src)
 {
-    a = i * BVH_LEAF;
-    b = min(n, a + BVH_LEAF);
+    return make_float4(__shfl_sync(FULLW, a.x, src), __shfl_sync(FULLW, a.y, src), __shfl_sync(FULLW, a.z, src), 0.f);
 }
 
 struct WarpJobs {
-    const int *rank;   // per warp job: node rank
-    const int *q0;     // first member of the warp's 32 queries
-    const int *out;    // where lane 0's result goes (lane l writes out + l)
+    const int *rank;  // per warp job: node rank
+    const int *q0;    // first member of the job's 32 queries (a multiple of 32)
+    const int *out;   // where the first query's result goes (query j writes out + j)
     int64_t count;
 };
 
-// nearest-neighbour distances, one warp per job of 32 consecutive members
-__global__ void __launch_bounds__(PK_WARPS * 32) k_bvh_nn(LevelBufs L, WarpJobs J, NodeArrays nd,
-                                                          const int64_t *box_base, const Box6 *boxes,
-                                                          const float4 *wpos, const float4 *wvel, const float *R2,
-                                                          const float *STOP, float *out, rs_dev_status *st)
+// Nearest-neighbour distance of member q (coordinates pq, vq) among the
+// node's members P, Q (n of them), starting from the radius `best` (the own
+// leaf `own` already scanned).  Returns as soon as the radius drops below
+// `stop`.  `best` is warp-uniform throughout.
+__device__ __forceinline__ float w32_nn(const BvhView &V, const MemberStore &M, int n, int q, float4 pq, float4 vq,
+                        const Metric6 &met, float best, float stop, int own, int *si, float *sd, rs_dev_status *st,
+                        int node)
 {
-    __shared__ int stk_s[PK_WARPS][PK_STACK];
+    const int lane = lane_id();
+    if (V.H < 2 || best < stop) return best;
+    if (lane == 0) {
+        si[0] = (V.H - 1) << 24;
+        sd[0] = 0.f;
+    }
+    int sp = 1;
+    __syncwarp();
+    for (int it = 0; sp > 0 && it < (1 << 24); it++) {
+        sp--;
+        const int ent = si[sp];
+        const float elb = sd[sp];
+        __syncwarp();
+        if (elb > best * RS_PRUNE_SLACK) continue;
+        const int ch = (ent >> 24) - 1, i = ent & 0xffffff;
+        const int c = 32 * i + lane;
+        const bool ok = c < V.cnt[ch] && !(ch == 0 && c == own);
+        const float lb = ok ? point_box_d2(pq, vq, box_get(V.S, V.off[ch] + c), met) : INFINITY;
+        unsigned mask = __ballot_sync(FULLW, ok && lb <= best * RS_PRUNE_SLACK);
+        if (ch == 0) {
+            // the two nearest needed leaves at a time (their loads overlap)
+            while (mask) {
+                bool mine = (mask >> lane) & 1u;
+                unsigned key = mine ? ford(lb) : 0xffffffffu;
+                unsigned mn = __reduce_min_sync(FULLW, key);
+                const int s0 = __ffs(__ballot_sync(FULLW, mine && key == mn)) - 1;
+                mask &= ~(1u << s0);
+                int s1 = -1;
+                if (mask) {
+                    mine = (mask >> lane) & 1u;
+                    key = mine ? ford(lb) : 0xffffffffu;
+                    mn = __reduce_min_sync(FULLW, key);
+                    s1 = __ffs(__ballot_sync(FULLW, mine && key == mn)) - 1;
+                    mask &= ~(1u << s1);
+                }
+                const int m0 = (32 * i + s0) * BVH_LEAF + lane, m1 = (32 * i + s1) * BVH_LEAF + lane;
+                const bool v0 = m0 < n && m0 != q, v1 = s1 >= 0 && m1 < n && m1 != q;
+                float4 p0 = make_float4(0, 0, 0, 0), u0 = p0, p1 = p0, u1 = p0;
+                if (v0) mem_get(M, m0, p0, u0);
+                if (v1) mem_get(M, m1, p1, u1);
+                float d = v0 ? d2_32(pq, vq, p0, u0, met) : INFINITY;
+                if (v1) d = fminf(d, d2_32(pq, vq, p1, u1, met));
+                best = fminf(best, wmin(d));
+                if (best < stop) return best;
+                mask &= __ballot_sync(FULLW, lb <= best * RS_PRUNE_SLACK);
+            }
+            continue;
+        }
+        if (sp + __popc(mask) > W_STACK) {
+            if (lane == 0) dev_fail(st, DEV_OVERFLOW, 54, node);
+            return best;
+        }
+        while (mask) {
+            const bool mine = (mask >> lane) & 1u;
+            const unsigned key = mine ? ford(lb) : 0u;
+            const unsigned mx = __reduce_max_sync(FULLW, key);
+            const int src = __ffs(__ballot_sync(FULLW, mine && key == mx)) - 1;
+            if (lane == src) {
+                si[sp] = (ch << 24) | c;
+                sd[sp] = lb;
+            }
+            sp++;
+            mask &= ~(1u << src);
+        }
+        __syncwarp();
+    }
+    return best;
+}
+
+// nearest-neighbour distances, one warp per job of 32 consecutive members
+// (one leaf): the leaf is held in registers, one member per lane, and its 32
+// queries are searched one after another
+__global__ void __launch_bounds__(W_WARPS * 32) k_bvh_nn(LevelBufs L, WarpJobs J, NodeArrays nd,
+                                                         const int64_t *box_base, BoxStore B, MemberStore MS,
+                                                         const float *R2, const float *STOP, float *out,
+                                                         rs_dev_status *st)
+{
+    __shared__ int si_s[W_WARPS][W_STACK];
+    __shared__ float sd_s[W_WARPS][W_STACK];
     const int w = warp_id(), lane = lane_id();
-    const int64_t gw = (int64_t)blockIdx.x * PK_WARPS + w;
+    const int64_t gw = (int64_t)blockIdx.x * W_WARPS + w;
     if (gw >= J.count) return;
     const int k = J.rank[gw], q0 = J.q0[gw];
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
     if (q0 >= n) return;
     const Metric6 met = L.met[k];
     BvhView V;
-    bvh_view(V, boxes + box_base[k], n);
-    const int q = q0 + lane;
-    const bool valid = q < n;
-    const float4 pq = valid ? wpos[first + q] : make_float4(0, 0, 0, 0);
-    const float4 vq = valid ? wvel[first + q] : make_float4(0, 0, 0, 0);
+    bvh_view(V, B, box_base[k], n);
+    const MemberStore M = mem_shift(MS, first);
     // start from the node's radius when one is given (just above it, so a
     // result at or above the start means "nothing within the radius")
     const float start = R2 ? R2[k] * 1.00000095367431640625f : INFINITY;
-    // a lane whose best falls below the stop value is done: its member is
+    // a query whose radius falls below the stop value is done: its member is
     // certainly below the linking length and its exact value is not needed
     const float stop = STOP ? STOP[k] : 0.f;
-    float best = start;
-    // the leaves holding the warp's own members first (a tight starting bound)
-    const int e = min(n, q0 + 32);
-    const int own0 = q0 / BVH_LEAF, own1 = (e - 1) / BVH_LEAF;
-    {
-        const int a = own0 * BVH_LEAF, b = min(n, (own1 + 1) * BVH_LEAF);
-        for (int m = a; m < b; m++) {
-            const float4 pc = wpos[first + m], vc = wvel[first + m];
-            if (valid && m != q) best = fminf(best, d2_32(pq, vq, pc, vc, met));
-        }
+    const int own = q0 / BVH_LEAF;
+    const int mo = q0 + lane;
+    const bool have = mo < n;
+    float4 po = make_float4(0, 0, 0, 0), vo = po;
+    if (have) mem_get(M, mo, po, vo);
+    const int nq = min(32, n - q0);
+    float res = INFINITY;
+    for (int j = 0; j < nq; j++) {
+        const float4 pq = shfl4(po, j), vq = shfl4(vo, j);
+        const float d = (have && lane != j) ? d2_32(pq, vq, po, vo, met) : INFINITY;
+        float best = fminf(start, wmin(d));
+        best = w32_nn(V, M, n, q0 + j, pq, vq, met, best, stop, own, si_s[w], sd_s[w], st, node);
+        if (lane == j) res = best;
     }
-    int *stk = stk_s[w];
-    if (lane == 0) stk[0] = ((V.H - 1) << 24) | 0;
-    int sp = 1;
-    __syncwarp();
-    for (int it = 0; sp > 0 && it < (1 << 26); it++) {
-        const int ent = stk[--sp];
-        __syncwarp();
-        const int h = ent >> 24, i = ent & 0xffffff;
-        const Box6 bx = V.bx[V.off[h] + i];
-        const bool live = valid && !(best < stop);
-        if (!__any_sync(0xffffffffu, live)) break;
-        const bool need = live && point_box_d2(pq, vq, bx, met) <= best * RS_PRUNE_SLACK;
-        if (!__any_sync(0xffffffffu, need)) continue;
-        if (h == 0) {
-            if (i >= own0 && i <= own1) continue;
-            int a, b;
-            leaf_range(i, n, a, b);
-            for (int m = a; m < b; m++) {
-                const float4 pc = wpos[first + m], vc = wvel[first + m];
-                if (need) best = fminf(best, d2_32(pq, vq, pc, vc, met));
-            }
-            continue;
-        }
-        // children some lane can still use, the nearer (for the warp) visited first
-        const int cprev = bvh_count(V.nl, h - 1);
-        const int c0 = 2 * i, c1 = 2 * i + 1;
-        const Box6 b0 = V.bx[V.off[h - 1] + c0];
-        const float d0 = live ? point_box_d2(pq, vq, b0, met) : INFINITY;
-        float d1 = INFINITY;
-        if (c1 < cprev) {
-            const Box6 b1 = V.bx[V.off[h - 1] + c1];
-            d1 = live ? point_box_d2(pq, vq, b1, met) : INFINITY;
-        }
-        const float lim = best * RS_PRUNE_SLACK;
-        const bool u0 = __any_sync(0xffffffffu, d0 <= lim), u1 = __any_sync(0xffffffffu, d1 <= lim);
-        const float s0 = warp_sum(live ? fminf(d0, 1e30f) : 0.f), s1 = warp_sum(live ? fminf(d1, 1e30f) : 0.f);
-        const bool first0 = s0 <= s1;  // push the farther first
-        const int nc = (u0 ? 1 : 0) + (u1 ? 1 : 0);
-        if (sp + nc > PK_STACK) {
-            if (lane == 0) dev_fail(st, DEV_OVERFLOW, 54, node);
-            break;
-        }
-        if (lane == 0) {
-            int t = sp;
-            if (first0) {
-                if (u1) stk[t++] = ((h - 1) << 24) | c1;
-                if (u0) stk[t++] = ((h - 1) << 24) | c0;
-            } else {
-                if (u0) stk[t++] = ((h - 1) << 24) | c0;
-                if (u1) stk[t++] = ((h - 1) << 24) | c1;
-            }
-        }
-        sp += nc;
-        __syncwarp();
-    }
-    if (valid) out[J.out[gw] + lane] = best >= start ? INFINITY : best;
+    if (have) out[J.out[gw] + lane] = res >= start ? INFINITY : res;
 }
 
-// nearest-neighbour distance of single sampled members (one thread each,
-// its own stack): the sample members are spread over the node, so they do not
-// share a traversal
-__global__ void __launch_bounds__(256) k_bvh_nn_sample(LevelBufs L, NodeArrays nd, const int64_t *box_base,
-                                                       const Box6 *boxes, const float4 *wpos, const float4 *wvel,
-                                                       const int64_t *soff, float *out, rs_dev_status *st)
+// nearest-neighbour distance of single sampled members, one warp each
+__global__ void __launch_bounds__(W_WARPS * 32) k_bvh_nn_sample(LevelBufs L, NodeArrays nd, const int64_t *box_base,
+                                                                BoxStore B, MemberStore MS, const int64_t *soff,
+                                                                float *out, rs_dev_status *st)
 {
+    __shared__ int si_s[W_WARPS][W_STACK];
+    __shared__ float sd_s[W_WARPS][W_STACK];
+    const int w = warp_id(), lane = lane_id();
     const int k = blockIdx.y;
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
     const int S = (int)(soff[k + 1] - soff[k]);
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.x * W_WARPS + w;
     if (s >= S) return;
     const int q = (int)(((int64_t)s * n) / S);
     const Metric6 met = L.met[k];
     BvhView V;
-    bvh_view(V, boxes + box_base[k], n);
-    const float4 pq = wpos[first + q], vq = wvel[first + q];
-    float best = INFINITY;
-    int stk[BVH_STACK];
-    float slb[BVH_STACK];
-    int sp = 0;
-    stk[sp] = ((V.H - 1) << 24) | 0;
-    slb[sp++] = 0.f;
-    for (int it = 0; sp > 0 && it < (1 << 26); it++) {
-        sp--;
-        if (slb[sp] > best * RS_PRUNE_SLACK) continue;
-        const int e = stk[sp];
-        const int h = e >> 24, i = e & 0xffffff;
-        if (h == 0) {
-            int a, b;
-            leaf_range(i, n, a, b);
-            for (int m = a; m < b; m++)
-                if (m != q) best = fminf(best, d2_32(pq, vq, wpos[first + m], wvel[first + m], met));
-            continue;
-        }
-        const int cprev = bvh_count(V.nl, h - 1);
-        const int c0 = 2 * i, c1 = 2 * i + 1;
-        const float l0 = point_box_d2(pq, vq, V.bx[V.off[h - 1] + c0], met);
-        const float l1 = c1 < cprev ? point_box_d2(pq, vq, V.bx[V.off[h - 1] + c1], met) : INFINITY;
-        const bool n0 = l0 <= l1;
-        const int fa = n0 ? c1 : c0, ne = n0 ? c0 : c1;
-        const float lfa = n0 ? l1 : l0, lne = n0 ? l0 : l1;
-        const float lim = best * RS_PRUNE_SLACK;
-        if (sp + 2 > BVH_STACK) {
-            dev_fail(st, DEV_OVERFLOW, 57, node);
-            break;
-        }
-        if (lfa <= lim) {
-            stk[sp] = ((h - 1) << 24) | fa;
-            slb[sp++] = lfa;
-        }
-        if (lne <= lim) {
-            stk[sp] = ((h - 1) << 24) | ne;
-            slb[sp++] = lne;
-        }
-    }
-    out[soff[k] + s] = best;
+    bvh_view(V, B, box_base[k], n);
+    const MemberStore M = mem_shift(MS, first);
+    float4 pq, vq, pm = make_float4(0, 0, 0, 0), vm = pm;
+    mem_get(M, q, pq, vq);
+    const int own = q / BVH_LEAF, m = own * BVH_LEAF + lane;
+    if (m < n) mem_get(M, m, pm, vm);
+    const float d = (m < n && m != q) ? d2_32(pq, vq, pm, vm, met) : INFINITY;
+    const float best = w32_nn(V, M, n, q, pq, vq, met, wmin(d), 0.f, own, si_s[w], sd_s[w], st, node);
+    if (lane == 0) out[soff[k] + s] = best;
 }
 
-// friends-of-friends at l, one warp per 32 consecutive members, pairs with
-// the candidate after the query in the node's member order
-__global__ void __launch_bounds__(PK_WARPS * 32) k_bvh_link(LevelBufs L, NodeArrays nd, const int64_t *box_base,
-                                                            const Box6 *boxes, const float4 *wpos,
-                                                            const float4 *wvel, const float *dnn, int *parent,
-                                                            rs_dev_status *st)
+// linking limits of one node: float32 band edges around l^2 (decided in
+// float64 inside them), the reporting band for ties, and the pruning radius
+struct LinkLim {
+    float lo, hi, tlo, thi, part, lim, cl_lim;
+    double l2, l;
+};
+
+__device__ __forceinline__ LinkLim link_lim(double l2)
 {
-    __shared__ int stk_s[PK_WARPS][PK_STACK];
+    LinkLim r;
+    r.l2 = l2;
+    r.l = sqrt(l2);
+    r.lo = (float)(l2 * (1.0 - RS_BAND));
+    r.hi = (float)(l2 * (1.0 + RS_BAND));
+    r.tlo = (float)(l2 * (1.0 - 3e-6));
+    r.thi = (float)(l2 * (1.0 + 3e-6));
+    r.part = fmaxf(r.hi, r.thi);
+    r.lim = r.part * RS_PRUNE_SLACK;
+    r.cl_lim = (float)(l2 * RS_CLIQUE_MARGIN);
+    return r;
+}
+
+// one candidate pair: bit 0 set when it is within l (decided in float64
+// inside the band), bit 1 set for a pair within 1e-6 (relative) of l but not
+// at it
+__device__ __forceinline__ int pair_test(const LinkLim &lm, const Metric6 &met, float4 pa, float4 va, float4 pb,
+                                         float4 vb)
+{
+    const float d2 = d2_32(pa, va, pb, vb, met);
+    if (d2 > lm.part) return 0;
+    if (d2 <= lm.lo) return 1;
+    if (d2 <= lm.hi || (d2 >= lm.tlo && d2 <= lm.thi)) {
+        const double e64 = d2_64(pa, va, pb, vb, met);
+        const int tie = (lm.l2 > 0 && e64 != lm.l2 && fabs(sqrt(e64) - lm.l) <= 1e-6 * lm.l) ? 2 : 0;
+        return (e64 <= lm.l2 ? 1 : 0) | tie;
+    }
+    return 0;
+}
+
+// Join a and b; returns the smaller of the two roots it joined (a member of
+// the merged set).
+__device__ __forceinline__ int uf_union_root(int *parent, int a, int b, rs_dev_status *st)
+{
+    for (int it = 0; it < RS_SPIN_LIMIT; it++) {
+        a = uf_find(parent, a, st);
+        b = uf_find(parent, b, st);
+        if (a == b) return a;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicCAS(&parent[b], b, a);
+        if (old == b) return a;
+        b = old;
+    }
+    dev_fail(st, DEV_TIMEOUT, 2, a);
+    return a;
+}
+
+// Join the query's set with friend b.  `rq` is a member known to be in the
+// query's set (sets only grow, so it stays one): when b's parent is rq the
+// two are joined already and the union is skipped.  Dense regions give each
+// query many friends whose parent is the set's root, so most unions end at
+// this one load.  Returns a member of the merged set, or INT_MAX when skipped.
+__device__ __forceinline__ int join_friend(int *parent, int a, int b, int rq, rs_dev_status *st)
+{
+    if (__ldcg(&parent[b]) == rq) return 0x7fffffff;
+    return uf_union_root(parent, a, b, st);
+}
+
+// Child c = 32 i + lane of stack entry `ent` for a friends-of-friends search
+// of member q: true when the child can hold a friend after q (its member
+// range extends past q + 1 and its box is within reach).  A clique box wholly
+// within reach is joined with one union and not searched.
+__device__ __forceinline__ bool link_child(const BvhView &V, int ent, int lane, int q, int own, float4 pq, float4 vq,
+                                           const Metric6 &met, const LinkLim &lm, int *parent, int first, int rq,
+                                           rs_dev_status *st)
+{
+    if (ent < 0) return false;
+    const int ch = (ent >> 24) - 1, c = 32 * (ent & 0xffffff) + lane;
+    if (!(c < V.cnt[ch] && !(ch == 0 && c == own) && bvh_m0(ch, c + 1) > (int64_t)q + 1)) return false;
+    const int64_t bi = V.off[ch] + c;
+    const Box6 bx = box_get(V.S, bi);
+    if (!(point_box_d2(pq, vq, bx, met) <= lm.lim)) return false;
+    if (V.S.cl[bi] && point_box_far2(pq, vq, bx, met) <= lm.cl_lim) {
+        join_friend(parent, first + q, first + (int)bvh_m0(ch, c), rq, st);
+        return false;
+    }
+    return true;
+}
+
+constexpr int LK_STACK = 256;  // link stack entries per warp
+constexpr int LK_LEAVES = 128; // pending leaves per warp
+constexpr int LK_BATCH = 4;    // leaves scanned together
+
+// Friends-of-friends pairs of member q with the members after it (outside
+// its own leaf) by a whole warp; returns this lane's tie count.  The search
+// pops two boxes at a time and collects the leaves within reach in a list,
+// which it scans LK_BATCH leaves at a time (one member per lane and leaf), so
+// several independent loads are in flight per warp.
+__device__ __forceinline__ int w32_link(const BvhView &V, const MemberStore &M, const float *D, int n,
+                                        int q, float4 pq, float4 vq, const Metric6 &met, const LinkLim &lm, int own,
+                                        int *parent, int first, int *si, int *lf, int &rq, rs_dev_status *st,
+                                        int node)
+{
+    const int lane = lane_id();
+    int tie = 0;
+    if (V.H < 2) return 0;
+    if (lane == 0) si[0] = (V.H - 1) << 24;
+    int sp = 1, nl = 0;
+    __syncwarp();
+    const unsigned below = (1u << lane) - 1u;
+    for (int it = 0; (sp > 0 || nl > 0) && it < (1 << 24); it++) {
+        if (sp > 0 && nl <= LK_LEAVES - 64) {
+            const int ea = si[sp - 1];
+            const int eb = sp >= 2 ? si[sp - 2] : -1;
+            __syncwarp();
+            sp -= eb >= 0 ? 2 : 1;
+            const bool na = link_child(V, ea, lane, q, own, pq, vq, met, lm, parent, first, rq, st);
+            const bool nb = link_child(V, eb, lane, q, own, pq, vq, met, lm, parent, first, rq, st);
+            const unsigned ma = __ballot_sync(FULLW, na), mb = __ballot_sync(FULLW, nb);
+            if (sp + __popc(ma) + __popc(mb) > LK_STACK) {
+                if (lane == 0) dev_fail(st, DEV_OVERFLOW, 55, node);
+                return tie;
+            }
+            const int ents[2] = {ea, eb};
+            const unsigned ms[2] = {ma, mb};
+            const bool nd2[2] = {na, nb};
+            for (int u = 0; u < 2; u++) {
+                if (!ms[u]) continue;
+                const int ch = (ents[u] >> 24) - 1, c = 32 * (ents[u] & 0xffffff) + lane;
+                const int slot = __popc(ms[u] & below);
+                if (ch == 0) {
+                    if (nd2[u]) lf[nl + slot] = c;
+                    nl += __popc(ms[u]);
+                } else {
+                    if (nd2[u]) si[sp + slot] = (ch << 24) | c;
+                    sp += __popc(ms[u]);
+                }
+            }
+            __syncwarp();
+            continue;
+        }
+        // scan the collected leaves
+        while (nl > 0) {
+            const int kk = min(nl, LK_BATCH);
+            nl -= kk;
+            int mm[LK_BATCH];
+#pragma unroll
+            for (int u = 0; u < LK_BATCH; u++) mm[u] = u < kk ? lf[nl + u] * BVH_LEAF + lane : -1;
+            __syncwarp();
+            float dd[LK_BATCH];
+            float4 pp[LK_BATCH], vv[LK_BATCH];
+#pragma unroll
+            for (int u = 0; u < LK_BATCH; u++) {
+                dd[u] = INFINITY;
+                if (mm[u] > q && mm[u] < n) {
+                    dd[u] = D[mm[u]];
+                    mem_get(M, mm[u], pp[u], vv[u]);
+                }
+            }
+            int nr = 0x7fffffff;
+#pragma unroll
+            for (int u = 0; u < LK_BATCH; u++) {
+                if (dd[u] <= lm.part) {
+                    const int r = pair_test(lm, met, pq, vq, pp[u], vv[u]);
+                    tie += r >> 1;
+                    if (r & 1) nr = min(nr, join_friend(parent, first + q, first + mm[u], rq, st));
+                }
+            }
+            rq = min(rq, (int)__reduce_min_sync(FULLW, (unsigned)nr));
+        }
+    }
+    return tie;
+}
+
+// friends-of-friends at l, one warp per leaf of 32 consecutive members, pairs
+// with the candidate after the query in the node's member order; only
+// members with a neighbour within reach take part
+__global__ void __launch_bounds__(TQ) k_bvh_link(LevelBufs L, NodeArrays nd, const int64_t *box_base,
+                                                 BoxStore B, MemberStore MS, const float *dnn, int *parent,
+                                                 rs_dev_status *st)
+{
+    __shared__ int si_s[TQ / 32][LK_STACK];
+    __shared__ int lf_s[TQ / 32][LK_LEAVES];
     const int w = warp_id(), lane = lane_id();
     const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x] + 32 * w;
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
     if (q0 >= n) return;
     const Metric6 met = L.met[k];
-    const double l2 = L.l2[k], l = sqrt(l2);
-    const float lo = (float)(l2 * (1.0 - RS_BAND)), hi = (float)(l2 * (1.0 + RS_BAND));
-    const float tlo = (float)(l2 * (1.0 - 3e-6)), thi = (float)(l2 * (1.0 + 3e-6));
-    const float part = fmaxf(hi, thi);
-    const float lim = part * RS_PRUNE_SLACK;
-    const float cl_lim = (float)(l2 * RS_CLIQUE_MARGIN);
-    const int q = q0 + lane;
-    const bool active = q < n && dnn[first + q] <= part;
-    if (!__any_sync(0xffffffffu, active)) return;
+    const LinkLim lm = link_lim(L.l2[k]);
+    const MemberStore M = mem_shift(MS, first);
+    const float *D = dnn + first;
+    const int mo = q0 + lane;
+    const bool have = mo < n;
+    const bool act = have && D[mo] <= lm.part;
+    unsigned rem = __ballot_sync(FULLW, act);
+    if (!rem) return;
+    float4 po = make_float4(0, 0, 0, 0), vo = po;
+    if (have) mem_get(M, mo, po, vo);
     BvhView V;
-    bvh_view(V, boxes + box_base[k], n);
-    const float4 pq = active ? wpos[first + q] : make_float4(0, 0, 0, 0);
-    const float4 vq = active ? wvel[first + q] : make_float4(0, 0, 0, 0);
+    bvh_view(V, B, box_base[k], n);
+    const int own = q0 / BVH_LEAF;
     int tie = 0;
-    int *stk = stk_s[w];
-    if (lane == 0) stk[0] = ((V.H - 1) << 24) | 0;
-    int sp = 1;
-    __syncwarp();
-    for (int it = 0; sp > 0 && it < (1 << 26); it++) {
-        const int ent = stk[--sp];
-        __syncwarp();
-        const int h = ent >> 24, i = ent & 0xffffff;
-        // boxes wholly before the warp's first query hold no candidate
-        if ((int64_t)(i + 1) * ((int64_t)BVH_LEAF << h) <= (int64_t)q0 + 1) continue;
-        const Box6 bx = V.bx[V.off[h] + i];
-        bool need = active && point_box_d2(pq, vq, bx, met) <= lim;
-        if (!__any_sync(0xffffffffu, need)) continue;
-        if (bx.phi.w != 0.f) {
-            // a clique box wholly within reach: one union with its first member
-            const bool covered = need && point_box_far2(pq, vq, bx, met) <= cl_lim;
-            if (covered) uf_union(parent, first + q, first + i * (BVH_LEAF << h), st);
-            need = need && !covered;
-            if (!__any_sync(0xffffffffu, need)) continue;
+    while (rem) {
+        const int j = __ffs(rem) - 1;
+        rem &= rem - 1;
+        const int q = q0 + j;
+        const float4 pq = shfl4(po, j), vq = shfl4(vo, j);
+        // a member of the query's set (its parent), refined as unions report roots
+        int rq = __ldcg(&parent[first + q]);
+        // pairs inside the own leaf, lane > j
+        int nr = 0x7fffffff;
+        if (lane > j && act) {
+            const int r = pair_test(lm, met, pq, vq, po, vo);
+            tie += r >> 1;
+            if (r & 1) nr = join_friend(parent, first + q, first + mo, rq, st);
         }
-        if (h == 0) {
-            int a, b;
-            leaf_range(i, n, a, b);
-            for (int m = max(a, q0 + 1); m < b; m++) {
-                const float dc = dnn[first + m];
-                if (dc > part) continue;
-                const float4 pc = wpos[first + m], vc = wvel[first + m];
-                if (!need || m <= q) continue;
-                const float d2 = d2_32(pq, vq, pc, vc, met);
-                if (d2 > part) continue;
-                bool link = d2 <= lo;
-                if (!link && (d2 <= hi || (d2 >= tlo && d2 <= thi))) {
-                    const double e64 = d2_64(pq, vq, pc, vc, met);
-                    link = e64 <= l2;
-                    if (l2 > 0 && e64 != l2 && fabs(sqrt(e64) - l) <= 1e-6 * l) tie++;
-                }
-                if (link) uf_union(parent, first + q, first + m, st);
-            }
-            continue;
-        }
-        const int cprev = bvh_count(V.nl, h - 1);
-        bool u[2] = {false, false};
-        for (int c = 0; c < 2; c++) {
-            const int ci = 2 * i + c;
-            if (ci >= cprev) break;
-            if ((int64_t)(ci + 1) * ((int64_t)BVH_LEAF << (h - 1)) <= (int64_t)q0 + 1) continue;
-            const Box6 cb = V.bx[V.off[h - 1] + ci];
-            u[c] = __any_sync(0xffffffffu, active && point_box_d2(pq, vq, cb, met) <= lim);
-        }
-        const int nc = (u[0] ? 1 : 0) + (u[1] ? 1 : 0);
-        if (sp + nc > PK_STACK) {
-            if (lane == 0) dev_fail(st, DEV_OVERFLOW, 55, node);
-            break;
-        }
-        if (lane == 0) {
-            int t = sp;
-            if (u[1]) stk[t++] = ((h - 1) << 24) | (2 * i + 1);
-            if (u[0]) stk[t++] = ((h - 1) << 24) | (2 * i);
-        }
-        sp += nc;
-        __syncwarp();
+        rq = min(rq, (int)__reduce_min_sync(FULLW, (unsigned)nr));
+        tie += w32_link(V, M, D, n, q, pq, vq, met, lm, own, parent, first, si_s[w], lf_s[w], rq, st, node);
     }
     tie = warp_sum(tie);
     if (lane == 0 && tie) atomicAdd(&L.tie[k], tie);
@@ -1609,8 +1820,23 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         RS_TRY(rs_scan_i64(ctx, bo, K + 1, tot + 2));
         int64_t NBX;
         RS_TRY(rs_read_i64(ctx, tot + 2, 1, &NBX, "rs_refine6d"));
-        RS_WS(ctx, Box6, boxes, WS_RF_HIST, NBX);
-        RS_LAUNCH(ctx, "rf_bvh_build", k_bvh_build, K, 256, 0, L, nd, (const int64_t *)bo, boxes,
+        RS_WS(ctx, char, boxmem, WS_RF_HIST, NBX * 49 + 1024);
+        BoxStore boxes;
+        {
+            char *bp2 = boxmem;
+            boxes.a = carve<float4>(bp2, NBX);
+            boxes.b = carve<float4>(bp2, NBX);
+            boxes.c = carve<float4>(bp2, NBX);
+            boxes.cl = carve<unsigned char>(bp2, NBX);
+        }
+        RS_WS(ctx, char, srch, WS_RF_SRCH, M * 24 + 512);
+        MemberStore ms;
+        {
+            char *sp2 = srch;
+            ms.a = carve<float4>(sp2, M);
+            ms.b = carve<float2>(sp2, M);
+        }
+        RS_LAUNCH(ctx, "rf_bvh_build", k_bvh_build, K, 256, 0, L, nd, (const int64_t *)bo, boxes, ms,
                   (const float4 *)wpos, (const float4 *)wvel);
         // ---- linking length: sampled bracket, bounded nearest neighbours, exact select ----
         RS_WS(ctx, int64_t, ch, WS_RF_MISC4, 2 * (K + 1) + 8);
@@ -1624,11 +1850,10 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         RS_WS(ctx, float, R2, WS_RF_R2, 2 * K + 8);
         float *STOP = R2 + K;
         if (SS > 0) {
-            dim3 grid((unsigned)ceil_div(SMP_MAX, 256), (unsigned)K);
+            dim3 grid((unsigned)ceil_div(SMP_MAX, W_WARPS), (unsigned)K);
             int pr = rs_prof_begin(ctx, "rf_smp_nn");
-            k_bvh_nn_sample<<<grid, 256, 0, ctx->stream>>>(L, nd, (const int64_t *)bo, (const Box6 *)boxes,
-                                                           (const float4 *)wpos, (const float4 *)wvel,
-                                                           (const int64_t *)nsm, sdnn, ctx->d_status);
+            k_bvh_nn_sample<<<grid, W_WARPS * 32, 0, ctx->stream>>>(L, nd, (const int64_t *)bo, boxes, ms,
+                                                                    (const int64_t *)nsm, sdnn, ctx->d_status);
             ctx->launches++;
             rs_prof_end(ctx, pr);
             RS_CUDA(ctx, cudaGetLastError());
@@ -1653,9 +1878,8 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         JF.count = W;
         RS_LAUNCH(ctx, "rf_full_jobs", k_full_jobs, K, 128, 0, (const int *)cur, (int)K, nd, (const int64_t *)nw, jf,
                   jf + W, jf + 2 * W);
-        RS_LAUNCH(ctx, "rf_lvl_nn", k_bvh_nn, ceil_div(W, PK_WARPS), PK_WARPS * 32, 0, L, JF, nd, (const int64_t *)bo,
-                  (const Box6 *)boxes, (const float4 *)wpos, (const float4 *)wvel, (const float *)R2,
-                  (const float *)STOP, dnn, ctx->d_status);
+        RS_LAUNCH(ctx, "rf_lvl_nn", k_bvh_nn, ceil_div(W, W_WARPS), W_WARPS * 32, 0, L, JF, nd, (const int64_t *)bo,
+                  boxes, ms, (const float *)R2, (const float *)STOP, dnn, ctx->d_status);
         RS_LAUNCH(ctx, "rf_lvl_initk", k_lvl_initk, ceil_div(K, 128), 128, 0, L, nd, f);
         for (int pass = 0; pass < 3; pass++) {
             RS_LAUNCH(ctx, "rf_lvl_hist", k_lvl_hist, T, TQ, 0, L, nd, (const float *)dnn, pass);
@@ -1667,9 +1891,9 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         RS_TRY(rs_read_i64(ctx, ctr + 6, 1, &fo, "rs_refine6d"));
         if ((fo >> 32) != 0) {
             // the bracket did not hold for some node: unbounded search
-            RS_LAUNCH(ctx, "rf_lvl_nn_full", k_bvh_nn, ceil_div(W, PK_WARPS), PK_WARPS * 32, 0, L, JF, nd,
-                      (const int64_t *)bo, (const Box6 *)boxes, (const float4 *)wpos, (const float4 *)wvel,
-                      (const float *)nullptr, (const float *)nullptr, dnn, ctx->d_status);
+            RS_LAUNCH(ctx, "rf_lvl_nn_full", k_bvh_nn, ceil_div(W, W_WARPS), W_WARPS * 32, 0, L, JF, nd,
+                      (const int64_t *)bo, boxes, ms, (const float *)nullptr, (const float *)nullptr, dnn,
+                      ctx->d_status);
             RS_LAUNCH(ctx, "rf_lvl_initk", k_lvl_initk, ceil_div(K, 128), 128, 0, L, nd, f);
             for (int pass = 0; pass < 3; pass++) {
                 RS_LAUNCH(ctx, "rf_lvl_hist", k_lvl_hist, T, TQ, 0, L, nd, (const float *)dnn, pass);
@@ -1686,8 +1910,8 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         RS_LAUNCH(ctx, "rf_lvl_l2", k_lvl_l2, K, 128, 0, L, nd, f, ctx->d_status);
         RS_LAUNCH(ctx, "rf_lvl_iota", k_lvl_iota, T, TQ, 0, L, nd, uf, csize, cmin);
         RS_LAUNCH(ctx, "rf_bvh_clique", k_bvh_clique, K, 256, 0, L, nd, (const int64_t *)bo, boxes, uf, ctx->d_status);
-        RS_LAUNCH(ctx, "rf_lvl_link", k_bvh_link, T, TQ, 0, L, nd, (const int64_t *)bo, (const Box6 *)boxes,
-                  (const float4 *)wpos, (const float4 *)wvel, (const float *)dnn, uf, ctx->d_status);
+        RS_LAUNCH(ctx, "rf_lvl_link", k_bvh_link, T, TQ, 0, L, nd, (const int64_t *)bo, boxes, ms,
+                  (const float *)dnn, uf, ctx->d_status);
         RS_LAUNCH(ctx, "rf_lvl_comp", k_lvl_comp, T, TQ, 0, L, nd, (const int *)widx, uf, csize, cmin,
                   ctx->d_status);
         // reorder: children first, by smallest particle index, then the rest
