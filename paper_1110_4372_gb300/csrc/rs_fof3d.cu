@@ -4,11 +4,14 @@
 // margin that covers the float32 rounding of the cell index), so any two
 // particles of one fine cell are friends and a fine cell can stand for all
 // of its particles in the union-find.  Fine cells are grouped 4 x 4 x 4 into
-// coarse cells; particles are radix-sorted by (coarse cell, fine sub-cell)
-// and a dense table maps each coarse cell to its first fine cell.  Every
-// friend of a particle lies within two fine cells per axis, which is inside
-// at most 2 x 2 x 2 coarse cells.  Two fine cells are joined as soon as one
-// pair between them is within l; pairs already in one set are skipped.
+// coarse cells; particles are radix-sorted by (coarse cell, fine sub-cell),
+// a dense table maps each coarse cell to its first fine cell, and a 64-bit
+// mask stored at that first fine cell tells which of the 64 sub-cells are
+// occupied.  Every friend of a particle lies within two fine cells per axis,
+// which is inside at most 2 x 2 x 2 coarse cells; the fine cells within
+// reach of a fine cell follow from the masks by bit operations, and their
+// indices by a popcount, with no scan.  Two fine cells are joined as soon as
+// one pair between them is within l; pairs already in one set are skipped.
 //
 // Distances: float32 with the periodic shift applied to the coordinate near
 // the top of the box (x - box is exact there), compared against l^2 (1 -+
@@ -96,6 +99,16 @@ __global__ void k_fof_cells(int64_t n, const uint64_t *keys, const uint32_t *sca
     if (q == n - 1) cell_start[*n_cells] = (uint32_t)n;
 }
 
+// occupancy mask of each coarse cell, kept at its first fine cell
+__global__ void k_fof_occ(const uint32_t *n_cells_p, const uint64_t *cell_key, const uint32_t *table, uint64_t *occ)
+{
+    const int64_t M = *n_cells_p;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < M; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = cell_key[c];
+        atomicOr((unsigned long long *)&occ[table[k >> 6]], 1ull << (k & 63));
+    }
+}
+
 __global__ void k_fill_u32(uint32_t *p, int64_t n, uint32_t v)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -109,17 +122,34 @@ __global__ void k_iota_i32(int *p, int64_t n)
     if (i < n) p[i] = (int)i;
 }
 
-__device__ __forceinline__ void cell_coords(uint64_t key, int Gc, int &fx, int &fy, int &fz)
+// sub-cells (4 per axis, bit (z << 4) | (y << 2) | x) of the coarse cell at
+// coarse offset d (per axis) whose fine offset from sub-cell u of the query's
+// coarse cell is at most R on every axis
+__device__ __forceinline__ unsigned axis_range(int u, int d, int R)
 {
-    uint64_t c = key >> 6;
-    int sub = (int)(key & 63);
-    int cx = (int)(c % (uint64_t)Gc);
-    uint64_t r = c / (uint64_t)Gc;
-    int cy = (int)(r % (uint64_t)Gc);
-    int cz = (int)(r / (uint64_t)Gc);
-    fx = 4 * cx + (sub & 3);
-    fy = 4 * cy + ((sub >> 2) & 3);
-    fz = 4 * cz + ((sub >> 4) & 3);
+    const int lo = max(u - R - 4 * d, 0), hi = min(u + R - 4 * d, 3);
+    return lo > hi ? 0u : ((2u << hi) - 1u) & ~((1u << lo) - 1u);
+}
+
+__device__ __forceinline__ uint64_t reach_mask(int ux, int uy, int uz, int dx, int dy, int dz, int R)
+{
+    const unsigned mx = axis_range(ux, dx, R), my = axis_range(uy, dy, R), mz = axis_range(uz, dz, R);
+    unsigned m16 = 0;
+    for (int y = 0; y < 4; y++)
+        if ((my >> y) & 1u) m16 |= mx << (4 * y);
+    uint64_t m = 0;
+    for (int z = 0; z < 4; z++)
+        if ((mz >> z) & 1u) m |= (uint64_t)m16 << (16 * z);
+    return m;
+}
+
+__device__ __forceinline__ void coarse_coords(uint64_t c, int Gc, int &cx, int &cy, int &cz)
+{
+    const uint32_t cc = (uint32_t)c, G = (uint32_t)Gc;  // fewer than 2^32 coarse cells
+    const uint32_t r = cc / G;
+    cx = (int)(cc - r * G);
+    cz = (int)(r / G);
+    cy = (int)(r - (uint32_t)cz * G);
 }
 
 // wrapped fine-cell offset b - a in [-Gf/2, Gf/2); shift tells which point
@@ -171,20 +201,22 @@ __device__ __forceinline__ int pair_link(const float4 &pa, const float4 &pb, int
 // takes the 26 adjacent cells (offsets of at most 1 per axis), where pairs are
 // friends almost at once in dense regions; pass 1 takes the cells two apart
 // on some axis, by which time dense regions are mostly one set and the
-// same-set check skips them.
-__global__ void __launch_bounds__(FOF_THREADS) k_fof_link(int64_t n_cells_cap, const uint32_t *n_cells_p,
-                                                            const uint64_t *cell_key, const uint32_t *cell_start,
-                                                            const uint32_t *table, const float4 *spos, int *parent,
+// same-set check skips them.  Coarse cells numbered below the query's hold
+// only fine cells of smaller index and are not visited.
+__global__ void __launch_bounds__(FOF_THREADS) k_fof_link(const uint32_t *n_cells_p, const uint64_t *cell_key,
+                                                            const uint32_t *cell_start, const uint32_t *table,
+                                                            const uint64_t *occ, const float4 *spos, int *parent,
                                                             FofGeom g, int pass, rs_dev_status *st)
 {
     const int64_t M = *n_cells_p;
     for (int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; A < M; A += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t ka = cell_key[A];
-        int ax, ay, az;
-        cell_coords(ka, g.Gc, ax, ay, az);
+        const uint64_t ka = cell_key[A], ca = ka >> 6;
+        const int sa = (int)(ka & 63), ux = sa & 3, uy = (sa >> 2) & 3, uz = sa >> 4;
+        int ccx, ccy, ccz;
+        coarse_coords(ca, g.Gc, ccx, ccy, ccz);
+        const int ax = 4 * ccx + ux, ay = 4 * ccy + uy, az = 4 * ccz + uz;
         const uint32_t a0 = cell_start[A], a1 = cell_start[A + 1];
-        const int ccx = ax >> 2, ccy = ay >> 2, ccz = az >> 2;
-        const int lox = (ax & 3) < 2 ? -1 : 0, loy = (ay & 3) < 2 ? -1 : 0, loz = (az & 3) < 2 ? -1 : 0;
+        const int lox = ux < 2 ? -1 : 0, loy = uy < 2 ? -1 : 0, loz = uz < 2 ? -1 : 0;
         for (int dz = loz; dz <= loz + 1; dz++) {
             int cz = ccz + dz;
             cz = cz < 0 ? cz + g.Gc : (cz >= g.Gc ? cz - g.Gc : cz);
@@ -195,18 +227,22 @@ __global__ void __launch_bounds__(FOF_THREADS) k_fof_link(int64_t n_cells_cap, c
                     int cx = ccx + dx;
                     cx = cx < 0 ? cx + g.Gc : (cx >= g.Gc ? cx - g.Gc : cx);
                     const uint64_t cc = ((uint64_t)cz * g.Gc + cy) * g.Gc + cx;
+                    if (cc < ca) continue;  // only fine cells of smaller index
                     const uint32_t b0c = table[cc];
                     if (b0c == 0xffffffffu) continue;
-                    for (int64_t B = b0c; B < M && (cell_key[B] >> 6) == cc; B++) {
-                        if (B <= A) continue;
-                        int bx, by, bz;
-                        cell_coords(cell_key[B], g.Gc, bx, by, bz);
+                    const uint64_t om = occ[b0c];
+                    const uint64_t near = reach_mask(ux, uy, uz, dx, dy, dz, 1);
+                    uint64_t cand = om & (pass == 0 ? near : reach_mask(ux, uy, uz, dx, dy, dz, 2) & ~near);
+                    if (cc == ca) cand &= ~((2ull << sa) - 1ull);  // sub-cells after A's
+                    while (cand) {
+                        const int sb = __ffsll((long long)cand) - 1;
+                        cand &= cand - 1ull;
+                        const int64_t B = (int64_t)b0c + __popcll(om & ((1ull << sb) - 1ull));
+                        const int bx = 4 * cx + (sb & 3), by = 4 * cy + ((sb >> 2) & 3), bz = 4 * cz + (sb >> 4);
                         int sx, sy, sz;
-                        int ox = fine_offset(ax, bx, g.Gf, sx), oy = fine_offset(ay, by, g.Gf, sy),
-                            oz = fine_offset(az, bz, g.Gf, sz);
-                        if (ox < -2 || ox > 2 || oy < -2 || oy > 2 || oz < -2 || oz > 2) continue;
-                        const bool adjacent = ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1;
-                        if (adjacent != (pass == 0)) continue;
+                        fine_offset(ax, bx, g.Gf, sx);
+                        fine_offset(ay, by, g.Gf, sy);
+                        fine_offset(az, bz, g.Gf, sz);
                         if (uf_find(parent, (int)A, st) == uf_find(parent, (int)B, st)) continue;
                         const uint32_t b0 = cell_start[B], b1 = cell_start[B + 1];
                         bool linked = false;
@@ -260,34 +296,43 @@ __global__ void k_fof_count_roots(const uint32_t *n_cells_p, const int *parent, 
 // reach whose float64 distance satisfies |d - l| <= 1e-6 l.
 __global__ void __launch_bounds__(FOF_THREADS) k_fof_tieband(const uint32_t *n_cells_p, const uint64_t *cell_key,
                                                                const uint32_t *cell_start, const uint32_t *table,
-                                                               const float4 *spos, FofGeom g,
+                                                               const uint64_t *occ, const float4 *spos, FofGeom g,
                                                                unsigned long long *count)
 {
     const int64_t M = *n_cells_p;
     const float flo = (float)(g.l2 * (1.0 - 4e-6)), fhi = (float)(g.l2 * (1.0 + 4e-6));
     unsigned long long c = 0;
     for (int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; A < M; A += (int64_t)gridDim.x * blockDim.x) {
-        int ax, ay, az;
-        cell_coords(cell_key[A], g.Gc, ax, ay, az);
+        const uint64_t ka = cell_key[A], ca = ka >> 6;
+        const int sa = (int)(ka & 63), ux = sa & 3, uy = (sa >> 2) & 3, uz = sa >> 4;
+        int ccx, ccy, ccz;
+        coarse_coords(ca, g.Gc, ccx, ccy, ccz);
+        const int ax = 4 * ccx + ux, ay = 4 * ccy + uy, az = 4 * ccz + uz;
         const uint32_t a0 = cell_start[A], a1 = cell_start[A + 1];
-        const int lox = (ax & 3) < 2 ? -1 : 0, loy = (ay & 3) < 2 ? -1 : 0, loz = (az & 3) < 2 ? -1 : 0;
+        const int lox = ux < 2 ? -1 : 0, loy = uy < 2 ? -1 : 0, loz = uz < 2 ? -1 : 0;
         for (int dz = loz; dz <= loz + 1; dz++)
             for (int dy = loy; dy <= loy + 1; dy++)
                 for (int dx = lox; dx <= lox + 1; dx++) {
-                    int cx = (ax >> 2) + dx, cy = (ay >> 2) + dy, cz = (az >> 2) + dz;
+                    int cx = ccx + dx, cy = ccy + dy, cz = ccz + dz;
                     cx = cx < 0 ? cx + g.Gc : (cx >= g.Gc ? cx - g.Gc : cx);
                     cy = cy < 0 ? cy + g.Gc : (cy >= g.Gc ? cy - g.Gc : cy);
                     cz = cz < 0 ? cz + g.Gc : (cz >= g.Gc ? cz - g.Gc : cz);
                     const uint64_t cc = ((uint64_t)cz * g.Gc + cy) * g.Gc + cx;
+                    if (cc < ca) continue;
                     const uint32_t b0c = table[cc];
                     if (b0c == 0xffffffffu) continue;
-                    for (int64_t B = b0c; B < M && (cell_key[B] >> 6) == cc; B++) {
-                        if (B < A) continue;
-                        int bx, by, bz, sx, sy, sz;
-                        cell_coords(cell_key[B], g.Gc, bx, by, bz);
-                        int ox = fine_offset(ax, bx, g.Gf, sx), oy = fine_offset(ay, by, g.Gf, sy),
-                            oz = fine_offset(az, bz, g.Gf, sz);
-                        if (ox < -2 || ox > 2 || oy < -2 || oy > 2 || oz < -2 || oz > 2) continue;
+                    const uint64_t om = occ[b0c];
+                    uint64_t cand = om & reach_mask(ux, uy, uz, dx, dy, dz, 2);
+                    if (cc == ca) cand &= ~((1ull << sa) - 1ull);  // A itself and the sub-cells after it
+                    while (cand) {
+                        const int sb = __ffsll((long long)cand) - 1;
+                        cand &= cand - 1ull;
+                        const int64_t B = (int64_t)b0c + __popcll(om & ((1ull << sb) - 1ull));
+                        const int bx = 4 * cx + (sb & 3), by = 4 * cy + ((sb >> 2) & 3), bz = 4 * cz + (sb >> 4);
+                        int sx, sy, sz;
+                        fine_offset(ax, bx, g.Gf, sx);
+                        fine_offset(ay, by, g.Gf, sy);
+                        fine_offset(az, bz, g.Gf, sz);
                         for (uint32_t i = a0; i < a1; i++) {
                             const float4 pa = spos[i];
                             for (uint32_t j = (B == A ? i + 1 : cell_start[B]); j < cell_start[B + 1]; j++) {
@@ -391,17 +436,21 @@ extern "C" rs_status rs_fof3d(rs_ctx *ctx, const float *pos, int32_t stride, int
     RS_LAUNCH(ctx, "fof_table_clear", k_fill_u32, fill_blocks, T, 0, table, ncoarse, 0xffffffffu);
     RS_LAUNCH(ctx, "fof_cells", k_fof_cells, nb, T, 0, n, (const uint64_t *)keys, (const uint32_t *)scan,
               (const uint32_t *)flag, cell_of, cell_start, cell_key, table, (const uint32_t *)n_cells);
+    RS_WS(ctx, uint64_t, occ, WS_FOF_OCC, n);
+    RS_CUDA(ctx, cudaMemsetAsync(occ, 0, sizeof(uint64_t) * n, ctx->stream));
+    const int64_t grid = std::min<int64_t>(nb, (int64_t)ctx->num_sms * 32);
+    RS_LAUNCH(ctx, "fof_occ", k_fof_occ, grid, T, 0, (const uint32_t *)n_cells, (const uint64_t *)cell_key,
+              (const uint32_t *)table, occ);
 
     RS_WS(ctx, int, parent, WS_FOF_PARENT, n);
     RS_WS(ctx, int, root_min, WS_FOF_ROOTMIN, n);
     RS_LAUNCH(ctx, "fof_iota", k_iota_i32, nb, T, 0, parent, n);
     RS_LAUNCH(ctx, "fof_fill", k_fill_u32, std::min<int64_t>(nb, (int64_t)ctx->num_sms * 16), T, 0,
               (uint32_t *)root_min, n, 0x7fffffffu);
-    const int64_t grid = std::min<int64_t>(nb, (int64_t)ctx->num_sms * 32);
     for (int pass = 0; pass < 2; pass++)
-        RS_LAUNCH(ctx, "fof_link", k_fof_link, grid, T, 0, n, (const uint32_t *)n_cells, (const uint64_t *)cell_key,
-                  (const uint32_t *)cell_start, (const uint32_t *)table, (const float4 *)spos, parent, g, pass,
-                  ctx->d_status);
+        RS_LAUNCH(ctx, "fof_link", k_fof_link, grid, T, 0, (const uint32_t *)n_cells, (const uint64_t *)cell_key,
+                  (const uint32_t *)cell_start, (const uint32_t *)table, (const uint64_t *)occ, (const float4 *)spos,
+                  parent, g, pass, ctx->d_status);
     RS_LAUNCH(ctx, "fof_rootmin", k_fof_rootmin, grid, T, 0, (const uint32_t *)n_cells,
               (const uint32_t *)cell_start, (const uint32_t *)idx, parent, root_min, ctx->d_status);
     RS_LAUNCH(ctx, "fof_labels", k_fof_labels, nb, T, 0, n, (const uint32_t *)idx, (const uint32_t *)cell_of,
@@ -415,7 +464,7 @@ extern "C" rs_status rs_fof3d(rs_ctx *ctx, const float *pos, int32_t stride, int
         if (n_tieband)
             RS_LAUNCH(ctx, "fof_tieband", k_fof_tieband, grid, T, 0, (const uint32_t *)n_cells,
                       (const uint64_t *)cell_key, (const uint32_t *)cell_start, (const uint32_t *)table,
-                      (const float4 *)spos, g, cnt + 1);
+                      (const uint64_t *)occ, (const float4 *)spos, g, cnt + 1);
         int64_t h[2];
         RS_TRY(rs_read_i64(ctx, cnt, 2, h, "rs_fof3d"));
         if (n_groups) *n_groups = h[0];

@@ -10,7 +10,7 @@
 // array that is part of the library image.
 //
 // The scratch is a file-scope __device__ array.  Every GPU that loads the
-// library holds it (about 9 MB) until the process exits.  In host code its
+// library holds it (about 10 MB) until the process exits.  In host code its
 // name is only a stand-in, not a device address, so the first call on each
 // device looks its address up with cudaGetSymbolAddress (with that device
 // current) and caches it; later calls on that device reuse the cached
@@ -47,11 +47,13 @@ constexpr int64_t SZ_CELLKEY = r256(8 * STATIC_MAX_N);
 constexpr int64_t SZ_TABLE = r256(4 * STATIC_MAX_CELLS);
 constexpr int64_t SZ_PARENT = r256(4 * STATIC_MAX_N);
 constexpr int64_t SZ_ROOTMIN = r256(4 * STATIC_MAX_N);
+constexpr int64_t SZ_OCC = r256(8 * STATIC_MAX_N);
 
 constexpr int64_t STATIC_BYTES = SZ_STATUS + 2 * SZ_K + 2 * SZ_V + SZ_HIST + SZ_SCAN + SZ_POS4 + SZ_MISC +
-                                 SZ_CELLOF + SZ_CELLSTART + SZ_CELLKEY + SZ_TABLE + SZ_PARENT + SZ_ROOTMIN;
+                                 SZ_CELLOF + SZ_CELLSTART + SZ_CELLKEY + SZ_TABLE + SZ_PARENT + SZ_ROOTMIN +
+                                 SZ_OCC;
 
-// The fixed scratch of rs_fof3d_static (about 9 MB).
+// The fixed scratch of rs_fof3d_static (about 10 MB).
 static __device__ __align__(256) unsigned char g_fof_scratch[STATIC_BYTES];
 
 constexpr int MAX_DEVICES = 64;
@@ -137,6 +139,7 @@ extern "C" rs_status rs_fof3d_static(const float *pos, int32_t stride, int64_t n
     take(WS_FOF_TABLE, SZ_TABLE);
     take(WS_FOF_PARENT, SZ_PARENT);
     take(WS_FOF_ROOTMIN, SZ_ROOTMIN);
+    take(WS_FOF_OCC, SZ_OCC);
     rs_dev_status h_status;
     int64_t h_scratch[64];
     c.h_status = &h_status;
