@@ -784,8 +784,30 @@ __device__ __forceinline__ void bvh_view(BvhView &V, const BoxStore &B, int64_t 
 // 8 ulps of the exact one), so all its members are joined once and a query
 // that reaches the whole box within the same margin joins it with a single
 // union.  These pairs lie strictly inside the linking length, never in the
-// tie band.  The flag is kept in the box's phi.w.
+// tie band.  The flag is kept in the box store's flag byte.
 #define RS_CLIQUE_MARGIN 0.99999237060546875  // 1 - 2^-17
+
+// linking limits of one node: float32 band edges around l^2 (decided in
+// float64 inside them), the reporting band for ties, and the pruning radius
+struct LinkLim {
+    float lo, hi, tlo, thi, part, lim, cl_lim;
+    double l2, l;
+};
+
+__device__ __forceinline__ LinkLim link_lim(double l2)
+{
+    LinkLim r;
+    r.l2 = l2;
+    r.l = sqrt(l2);
+    r.lo = (float)(l2 * (1.0 - RS_BAND));
+    r.hi = (float)(l2 * (1.0 + RS_BAND));
+    r.tlo = (float)(l2 * (1.0 - 3e-6));
+    r.thi = (float)(l2 * (1.0 + 3e-6));
+    r.part = fmaxf(r.hi, r.thi);
+    r.lim = r.part * RS_PRUNE_SLACK;
+    r.cl_lim = (float)(l2 * RS_CLIQUE_MARGIN);
+    return r;
+}
 
 __device__ __forceinline__ float box_diam2(const Box6 &b, const Metric6 &m)
 {
@@ -803,20 +825,58 @@ __device__ __forceinline__ float point_box_far2(float4 p, float4 v, const Box6 &
     return (fx * fx + fy * fy + fz * fz) * m.ax + (fu * fu + fv * fv + fw * fw) * m.av;
 }
 
-// one block per node: flag the clique boxes, then join the members of every
-// maximal one (a clique box whose parent is not a clique)
-__global__ void __launch_bounds__(256) k_bvh_clique(LevelBufs L, NodeArrays nd, const int64_t *box_base, BoxStore B,
-                                                    int *parent, rs_dev_status *st)
+// One block per node, once the linking length is known.  The boxes are
+// rebuilt over the members that can have a friend (nearest-neighbour value
+// within reach; the link search skips the others as candidates and as
+// queries), which drops the phase-space outliers that stretch them.  A box
+// whose members all can have a friend and whose diameter is within the
+// clique margin is flagged, and the members of every maximal flagged box (a
+// flagged box whose parent is not flagged) are joined.
+__global__ void __launch_bounds__(256) k_bvh_linkbox(LevelBufs L, NodeArrays nd, const int64_t *box_base, BoxStore B,
+                                                     const float4 *wpos, const float4 *wvel, const float *dnn,
+                                                     int *parent, rs_dev_status *st)
 {
     const int k = blockIdx.x;
     if (k >= L.K) return;
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
     const Metric6 met = L.met[k];
+    const LinkLim lm = link_lim(L.l2[k]);
     const float lim = (float)(L.l2[k] * RS_CLIQUE_MARGIN);
     BvhView V;
     bvh_view(V, B, box_base[k], n);
+    // leaves; the flag holds "every member can have a friend" until the end
+    for (int i = threadIdx.x; i < V.nl; i += blockDim.x) {
+        Box6 b = box_empty();
+        bool all = true;
+        const int e = min(n, (i + 1) * BVH_LEAF);
+        for (int m = i * BVH_LEAF; m < e; m++) {
+            if (dnn[first + m] <= lm.part)
+                box_add(b, wpos[first + m], wvel[first + m]);
+            else
+                all = false;
+        }
+        box_put(V.S, i, b);
+        V.S.cl[i] = all ? 1 : 0;
+    }
+    __syncthreads();
+    for (int h = 1; h < V.H; h++) {
+        const int cprev = V.cnt[h - 1];
+        for (int i = threadIdx.x; i < V.cnt[h]; i += blockDim.x) {
+            Box6 b = box_get(V.S, V.off[h - 1] + 32 * i);
+            bool all = V.S.cl[V.off[h - 1] + 32 * i] != 0;
+            const int e = min(cprev, 32 * i + 32);
+            for (int c = 32 * i + 1; c < e; c++) {
+                box_merge(b, box_get(V.S, V.off[h - 1] + c));
+                all = all && V.S.cl[V.off[h - 1] + c] != 0;
+            }
+            box_put(V.S, V.off[h] + i, b);
+            V.S.cl[V.off[h] + i] = all ? 1 : 0;
+        }
+        __syncthreads();
+    }
     const int total = V.off[V.H - 1] + 1;
-    for (int b = threadIdx.x; b < total; b += blockDim.x) V.S.cl[b] = box_diam2(box_get(V.S, b), met) <= lim ? 1 : 0;
+    for (int b = threadIdx.x; b < total; b += blockDim.x)
+        if (V.S.cl[b] && !(box_diam2(box_get(V.S, b), met) <= lim)) V.S.cl[b] = 0;
     __syncthreads();
     for (int b = threadIdx.x; b < total; b += blockDim.x) {
         if (!V.S.cl[b]) continue;
@@ -1004,28 +1064,6 @@ __global__ void __launch_bounds__(W_WARPS * 32) k_bvh_nn_sample(LevelBufs L, Nod
     const float d = (m < n && m != q) ? d2_32(pq, vq, pm, vm, met) : INFINITY;
     const float best = w32_nn(V, M, n, q, pq, vq, met, wmin(d), 0.f, own, si_s[w], sd_s[w], st, node);
     if (lane == 0) out[soff[k] + s] = best;
-}
-
-// linking limits of one node: float32 band edges around l^2 (decided in
-// float64 inside them), the reporting band for ties, and the pruning radius
-struct LinkLim {
-    float lo, hi, tlo, thi, part, lim, cl_lim;
-    double l2, l;
-};
-
-__device__ __forceinline__ LinkLim link_lim(double l2)
-{
-    LinkLim r;
-    r.l2 = l2;
-    r.l = sqrt(l2);
-    r.lo = (float)(l2 * (1.0 - RS_BAND));
-    r.hi = (float)(l2 * (1.0 + RS_BAND));
-    r.tlo = (float)(l2 * (1.0 - 3e-6));
-    r.thi = (float)(l2 * (1.0 + 3e-6));
-    r.part = fmaxf(r.hi, r.thi);
-    r.lim = r.part * RS_PRUNE_SLACK;
-    r.cl_lim = (float)(l2 * RS_CLIQUE_MARGIN);
-    return r;
 }
 
 // one candidate pair: bit 0 set when it is within l (decided in float64
@@ -1909,7 +1947,8 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
                   (const float4 *)wvel, (const float *)dnn);
         RS_LAUNCH(ctx, "rf_lvl_l2", k_lvl_l2, K, 128, 0, L, nd, f, ctx->d_status);
         RS_LAUNCH(ctx, "rf_lvl_iota", k_lvl_iota, T, TQ, 0, L, nd, uf, csize, cmin);
-        RS_LAUNCH(ctx, "rf_bvh_clique", k_bvh_clique, K, 256, 0, L, nd, (const int64_t *)bo, boxes, uf, ctx->d_status);
+        RS_LAUNCH(ctx, "rf_bvh_linkbox", k_bvh_linkbox, K, 256, 0, L, nd, (const int64_t *)bo, boxes,
+                  (const float4 *)wpos, (const float4 *)wvel, (const float *)dnn, uf, ctx->d_status);
         RS_LAUNCH(ctx, "rf_lvl_link", k_bvh_link, T, TQ, 0, L, nd, (const int64_t *)bo, boxes, ms,
                   (const float *)dnn, uf, ctx->d_status);
         RS_LAUNCH(ctx, "rf_lvl_comp", k_lvl_comp, T, TQ, 0, L, nd, (const int *)widx, uf, csize, cmin,
