@@ -50,6 +50,16 @@ BYTES_FOF_PER_PARTICLE = 16
 BYTES_LEVEL_PER_MEMBER = 28
 BYTES_ASSIGN_PER_MEMBER = 28
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per unit, from
+# one ncu capture of every launch of the kernel in one step of the 16.8M
+# workload (profiles/k_bvh_link_c3q_full.md, profiles/k_bvh_nn_c3q_full.md),
+# scaled to a step by the units processed.  An entry is dropped when its
+# kernel changes.
+NCU_TRAFFIC_PER_UNIT = {
+    "rf_lvl_link": 326767104 / 8612074,
+    "rf_lvl_nn": 244146944 / 8612074,
+}
+
 # Which units each kernel processes per step (for its algorithmic bytes).
 KERNEL_UNITS = {
     "fof_link": ("particles", BYTES_FOF_PER_PARTICLE),
@@ -312,8 +322,12 @@ def main():
     bytes_per_step = per_unit * units[unit_name]
     achieved = bytes_per_step * args.steps / (dom_ms * 1e-3) / 1e9
     peak = peaks["hbm_gbs"]
+    traffic = None
+    if dom_name in NCU_TRAFFIC_PER_UNIT:
+        traffic = NCU_TRAFFIC_PER_UNIT[dom_name] * units[unit_name]
     roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_kind": f"{peak_kind} (hbm_gbs)",
+                "frac": achieved / peak, "traffic": traffic, "traffic_per": "step (all launches)",
+                "peak_kind": f"{peak_kind} (hbm_gbs)",
                 "algorithmic_bytes_per_step": bytes_per_step, "unit_per_step": f"{units[unit_name]} {unit_name}",
                 "ms_per_step": dom_ms / args.steps, "share": dom_ms / total_ms if total_ms else None}
     b_alg = BYTES_FOF_PER_PARTICLE * n + BYTES_LEVEL_PER_MEMBER * stats["sum_level_members"]
