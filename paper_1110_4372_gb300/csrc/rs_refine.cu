@@ -6,11 +6,15 @@
 // group straddles a face).  Nodes own nested slot ranges: a node's children
 // occupy the front of its range.
 //
-// Two size classes:
+// Three size classes:
+//  * tiny nodes (<= TINY_N = 32 members): one warp holds the node in
+//    registers, a member per lane, and builds its whole subtree with warp
+//    shuffles and votes, eight subtrees per CTA at a time;
 //  * small nodes (<= SMALL_N members): one CTA loads the node into shared
 //    memory and builds its whole subtree there (moments, nearest neighbours,
 //    exact k-th select, union-find, children, recursion with an explicit
-//    stack), as a persistent work queue over all small nodes;
+//    stack), as a persistent work queue over all small nodes; tiny nodes it
+//    meets (roots or children) go to the tiny queue;
 //  * big nodes: processed level by level by tiles of 256 members spread over
 //    the whole GPU, with per-node accumulators and histograms in global
 //    memory; children above SMALL_N stay on the big path, smaller children
@@ -33,6 +37,9 @@ namespace {
 constexpr int SMALL_N = 1024;       // largest node handled by one CTA
 constexpr int SMALL_THREADS = 256;
 constexpr int STACK_CAP = 256;
+constexpr int TINY_N = 32;          // largest node handled by one warp
+constexpr int TINY_WARPS = 8;       // warps per block of the tiny-node kernel
+constexpr int TINY_STACK = 32;      // pending nodes per warp
 constexpr int TQ = 256;             // big-node tile (members per CTA)
 
 // ---------------------------------------------------------------------------
@@ -225,8 +232,8 @@ __device__ void bitonic_u64(unsigned long long *key, int P)
 }
 
 __global__ void __launch_bounds__(SMALL_THREADS, 2)
-    k_small_subtree(const int *queue, const int *queue_len, int *queue_head, const float4 *wpos, const float4 *wvel,
-                    int *widx, NodeArrays nd, double box, double f, int min_n, rs_dev_status *st)
+    k_small_subtree(const int *queue, const int *queue_len, int *queue_head, float4 *wpos, float4 *wvel, int *widx,
+                    int *tiny_q, int *tiny_len, NodeArrays nd, double box, double f, int min_n, rs_dev_status *st)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmallShared &S = *reinterpret_cast<SmallShared *>(smem_raw);
@@ -240,6 +247,10 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
         const int node0 = queue[job];
         const int base = nd.first[node0];
         const int n0 = nd.count[node0];
+        if (n0 <= TINY_N) {  // a tiny subtree: one warp of the tiny-node kernel
+            if (tid == 0) tiny_q[atomicAdd(tiny_len, 1)] = node0;
+            continue;
+        }
         for (int i = tid; i < n0; i += SMALL_THREADS) {
             float4 p = wpos[base + i], v = wvel[base + i];
             S.px[i] = p.x;
@@ -318,23 +329,29 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
             const float bhi = (float)((double)t32 * (1.0 + 2.0 * RS_BAND));
             __syncthreads();
             // ---- band members: exact float64 nearest-neighbour distances ----
+            // (one warp per band member, lanes over the candidates)
             double *bval = reinterpret_cast<double *>(S.key);
+            int *blist = S.tidx;
             for (int q = lf + tid; q < lf + cnt; q += SMALL_THREADS) {
                 const float dq = S.dnn[q];
-                if (dq < blo) {
+                if (dq < blo)
                     atomicAdd(&S.below, 1);
-                } else if (dq <= bhi) {
-                    const float4 pq = sp4(S, q), vq = sv4(S, q);
-                    const float lim = dq * (float)(1.0 + 2.0 * RS_BAND);
-                    double best = INFINITY;
-                    for (int c = lf; c < lf + cnt; c++) {
-                        if (c == q) continue;
-                        const float4 pc = sp4(S, c), vc = sv4(S, c);
-                        if (d2_32(pq, vq, pc, vc, met) <= lim) best = fmin(best, d2_64(pq, vq, pc, vc, met));
-                    }
-                    int slot = atomicAdd(&S.nband, 1);
-                    bval[slot] = best;
+                else if (dq <= bhi)
+                    blist[atomicAdd(&S.nband, 1)] = q;
+            }
+            __syncthreads();
+            for (int b = warp_id(); b < S.nband; b += SMALL_THREADS / 32) {
+                const int q = blist[b];
+                const float4 pq = sp4(S, q), vq = sv4(S, q);
+                const float lim = S.dnn[q] * (float)(1.0 + 2.0 * RS_BAND);
+                double best = INFINITY;
+                for (int c = lf + lane_id(); c < lf + cnt; c += 32) {
+                    if (c == q) continue;
+                    const float4 pc = sp4(S, c), vc = sv4(S, c);
+                    if (d2_32(pq, vq, pc, vc, met) <= lim) best = fmin(best, d2_64(pq, vq, pc, vc, met));
                 }
+                for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+                if (lane_id() == 0) bval[b] = best;
             }
             __syncthreads();
             // rank the band: the exact k-th value is the (k - 1 - below)-th
@@ -367,12 +384,18 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
                 const float part = fmaxf(hi, thi);
                 const double l = sqrt(l2);
                 int tie = 0;
-                for (int q = lf + tid; q < lf + cnt; q += SMALL_THREADS) {
-                    if (S.dnn[q] > part) continue;
-                    const float4 pq = sp4(S, q), vq = sv4(S, q);
-                    for (int c = q + 1; c < lf + cnt; c++) {
+                // warp-uniform candidate loop from the warp's first query: the
+                // candidate test and its loads are the same for every lane
+                for (int qb = lf + 32 * warp_id(); qb < lf + cnt; qb += SMALL_THREADS) {
+                    const int q = qb + lane_id();
+                    const bool act = q < lf + cnt && S.dnn[q] <= part;
+                    if (!__any_sync(0xffffffffu, act)) continue;
+                    const float4 pq = act ? sp4(S, q) : make_float4(0, 0, 0, 0);
+                    const float4 vq = act ? sv4(S, q) : make_float4(0, 0, 0, 0);
+                    for (int c = qb + 1; c < lf + cnt; c++) {
                         if (S.dnn[c] > part) continue;
                         const float4 pc = sp4(S, c), vc = sv4(S, c);
+                        if (!act || c <= q) continue;
                         const float d2 = d2_32(pq, vq, pc, vc, met);
                         if (d2 > part) continue;
                         bool link = d2 <= lo;
@@ -456,6 +479,10 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
                 nd.root[id] = nd.root[node];
                 nd.shift[id] = nd.shift[node];
                 atomicAdd(&S.nchild, 1);
+                if (e - p <= TINY_N) {  // its subtree goes to the tiny-node kernel
+                    tiny_q[atomicAdd(tiny_len, 1)] = id;
+                    continue;
+                }
                 int s = atomicAdd(&S.sp, 1);
                 if (s >= STACK_CAP) {
                     dev_fail(st, DEV_OVERFLOW, 42, s);
@@ -471,8 +498,244 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
             }
             __syncthreads();
         }
-        for (int i = tid; i < n0; i += SMALL_THREADS) widx[base + i] = S.idx[i];
+        // members in their final order (the tiny-node kernel reads its nodes here)
+        for (int i = tid; i < n0; i += SMALL_THREADS) {
+            widx[base + i] = S.idx[i];
+            wpos[base + i] = make_float4(S.px[i], S.py[i], S.pz[i], 0.f);
+            wvel[base + i] = make_float4(S.vx[i], S.vy[i], S.vz[i], 0.f);
+        }
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tiny nodes: whole subtree in one warp
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 shfl_xyz(float4 a, int src)
+{
+    return make_float4(__shfl_sync(0xffffffffu, a.x, src), __shfl_sync(0xffffffffu, a.y, src),
+                       __shfl_sync(0xffffffffu, a.z, src), 0.f);
+}
+
+// ascending bitonic sort of one 64-bit key per lane across the warp
+__device__ __forceinline__ unsigned long long warp_sort_u64(unsigned long long key)
+{
+    const int lane = lane_id();
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, key, j);
+            const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+            key = keep_min ? (o < key ? o : key) : (o > key ? o : key);
+        }
+    return key;
+}
+
+// One warp per tiny subtree: lane i holds member i of the subtree root's slot
+// range, and a node is a contiguous range of lanes.  The steps and their
+// arithmetic are those of the one-CTA path: exact moments, float32 nearest
+// neighbours, the float32 k-th value and the float64 band around it, the
+// float64 k-th value, friends-of-friends with the float64 recheck in the band,
+// then children first by smallest particle index and the rest after them.
+__global__ void __launch_bounds__(TINY_WARPS * 32)
+    k_tiny_subtree(const int *queue, const int *queue_len, int *queue_head, const float4 *wpos, const float4 *wvel,
+                   int *widx, NodeArrays nd, double box, double f, int min_n, rs_dev_status *st)
+{
+    __shared__ int par_s[TINY_WARPS][32];
+    __shared__ int csz_s[TINY_WARPS][32];
+    __shared__ int cmin_s[TINY_WARPS][32];
+    __shared__ int4 stk_s[TINY_WARPS][TINY_STACK];
+    const unsigned FULL = 0xffffffffu;
+    const int w = warp_id(), lane = lane_id();
+    int *par = par_s[w], *csz = csz_s[w], *cmn = cmin_s[w];
+    int4 *stk = stk_s[w];
+    const int qlen = *queue_len;
+    for (int guard = 0; guard < (1 << 30); guard++) {
+        int job = 0;
+        if (lane == 0) job = atomicAdd(queue_head, 1);
+        job = __shfl_sync(FULL, job, 0);
+        if (job >= qlen) break;
+        const int node0 = queue[job];
+        const int base = nd.first[node0], n0 = nd.count[node0];
+        if (n0 > TINY_N) {
+            if (lane == 0) dev_fail(st, DEV_INTERNAL, 44, node0);
+            continue;
+        }
+        float4 p = make_float4(0, 0, 0, 0), v = p;
+        int idx = 0x7fffffff;
+        if (lane < n0) {
+            p = wpos[base + lane];
+            v = wvel[base + lane];
+            idx = widx[base + lane];
+        }
+        if (lane == 0) stk[0] = make_int4(0, n0, node0, nd.level[node0]);
+        int sp = 1;
+        __syncwarp();
+        for (int it = 0; sp > 0 && it < 4096; it++) {
+            const int4 top = stk[--sp];
+            __syncwarp();
+            const int off = top.x, cnt = top.y, node = top.z, lev = top.w;
+            const bool mine = lane >= off && lane < off + cnt;
+            // ---- moments (exact), the node's first member as reference ----
+            const float4 pr = shfl_xyz(p, off), vr = shfl_xyz(v, off);
+            MomAcc a;
+            mom_zero(a);
+            if (mine) mom_add(a, p, v, mom_ref(pr, vr));
+            mom_warp_reduce(a);
+            Metric6 met;
+            {
+                double ax64 = 0, av64 = 0, scale = 0;
+                if (lane == 0) {
+                    const MomOut o = mom_finalize(a, pr, vr, cnt, box);
+                    for (int d = 0; d < 3; d++) {
+                        nd.xbar[3 * node + d] = o.xbar[d];
+                        nd.vbar[3 * node + d] = o.vbar[d];
+                    }
+                    nd.sigx[node] = o.sigx;
+                    nd.sigv[node] = o.sigv;
+                    const Metric6 m = metric_of(o.sigx, o.sigv);
+                    ax64 = m.ax64;
+                    av64 = m.av64;
+                    scale = m.scale;
+                }
+                met.ax64 = __shfl_sync(FULL, ax64, 0);
+                met.av64 = __shfl_sync(FULL, av64, 0);
+                met.scale = __shfl_sync(FULL, scale, 0);
+                met.ax = (float)met.ax64;
+                met.av = (float)met.av64;
+            }
+            // ---- nearest neighbours (float32) ----
+            float dnn = INFINITY;
+            for (int c = off; c < off + cnt; c++) {
+                const float4 pc = shfl_xyz(p, c), vc = shfl_xyz(v, c);
+                if (mine && c != lane) dnn = fminf(dnn, d2_32(p, v, pc, vc, met));
+            }
+            // ---- k-th smallest, float32: the member of rank k - 1 by (value, lane) ----
+            long long kk = (long long)ceil(f * (double)cnt);
+            if (kk < 1) kk = 1;
+            if (kk > cnt) kk = cnt;
+            int rank = 0;
+            for (int c = off; c < off + cnt; c++) {
+                const float dc = __shfl_sync(FULL, dnn, c);
+                if (mine && (dc < dnn || (dc == dnn && c < lane))) rank++;
+            }
+            const unsigned pick = __ballot_sync(FULL, mine && rank == kk - 1);
+            const float t32 = __shfl_sync(FULL, dnn, pick ? __ffs(pick) - 1 : off);
+            const float blo = (float)((double)t32 * (1.0 - 2.0 * RS_BAND));
+            const float bhi = (float)((double)t32 * (1.0 + 2.0 * RS_BAND));
+            // ---- band members: exact float64 nearest-neighbour distances ----
+            const bool inband = mine && dnn >= blo && dnn <= bhi;
+            const int below = __popc(__ballot_sync(FULL, mine && dnn < blo));
+            double ex = INFINITY;
+            if (__any_sync(FULL, inband)) {
+                const float lim = dnn * (float)(1.0 + 2.0 * RS_BAND);
+                for (int c = off; c < off + cnt; c++) {
+                    const float4 pc = shfl_xyz(p, c), vc = shfl_xyz(v, c);
+                    if (inband && c != lane && d2_32(p, v, pc, vc, met) <= lim) ex = fmin(ex, d2_64(p, v, pc, vc, met));
+                }
+            }
+            // the exact k-th value is the (k - 1 - below)-th smallest band value
+            const int want = (int)(kk - 1) - below;
+            const unsigned bmask = __ballot_sync(FULL, inband);
+            int brank = 0;
+            for (int c = off; c < off + cnt; c++) {
+                const double ec = __shfl_sync(FULL, ex, c);
+                if (inband && ((bmask >> c) & 1u) && (ec < ex || (ec == ex && c < lane))) brank++;
+            }
+            const unsigned bp = __ballot_sync(FULL, inband && brank == want);
+            if (!bp && lane == 0) dev_fail(st, DEV_INTERNAL, 45, node);
+            const double l2 = bp ? __shfl_sync(FULL, ex, __ffs(bp) - 1) : 0.0;
+            if (lane == 0) nd.lnk[node] = sqrt(l2 / met.scale);
+            // ---- friends-of-friends at l (inclusive) ----
+            const float lo = (float)(l2 * (1.0 - RS_BAND)), hi = (float)(l2 * (1.0 + RS_BAND));
+            const float tlo = (float)(l2 * (1.0 - 3e-6)), thi = (float)(l2 * (1.0 + 3e-6));
+            const float part = fmaxf(hi, thi);
+            const double l = sqrt(l2);
+            par[lane] = lane;
+            __syncwarp();
+            int tie = 0;
+            const bool act = mine && dnn <= part;
+            for (int c = off; c < off + cnt; c++) {
+                const float dc = __shfl_sync(FULL, dnn, c);
+                const float4 pc = shfl_xyz(p, c), vc = shfl_xyz(v, c);
+                if (!act || c <= lane || dc > part) continue;
+                const float d2 = d2_32(p, v, pc, vc, met);
+                if (d2 > part) continue;
+                bool link = d2 <= lo;
+                if (!link && (d2 <= hi || (d2 >= tlo && d2 <= thi))) {
+                    const double e = d2_64(p, v, pc, vc, met);
+                    link = e <= l2;
+                    if (l2 > 0 && e != l2 && fabs(sqrt(e) - l) <= 1e-6 * l) tie++;
+                }
+                if (link) uf_union_s(par, lane, c, st);
+            }
+            tie = warp_sum(tie);
+            __syncwarp();
+            // ---- components ----
+            csz[lane] = 0;
+            cmn[lane] = 0x7fffffff;
+            __syncwarp();
+            int r = lane;
+            if (mine) {
+                r = uf_find_s(par, lane);
+                atomicAdd(&csz[r], 1);
+                atomicMin(&cmn[r], idx);
+            }
+            __syncwarp();
+            // ---- children first (by smallest particle index), then the rest ----
+            unsigned hiw = 0xffffffffu;
+            if (mine) {
+                const int sz = csz[r];
+                if (sz >= min_n && sz < cnt) hiw = (unsigned)cmn[r];
+            }
+            const unsigned long long key =
+                warp_sort_u64(mine ? (((unsigned long long)hiw << 32) | (unsigned)(lane - off)) : ~0ull);
+            // the lane at position q of the node takes the member whose key sorted to q
+            const unsigned long long kq = __shfl_sync(FULL, key, mine ? lane - off : lane);
+            const int from = mine ? off + (int)(kq & 0xffffffffu) : lane;
+            p = shfl_xyz(p, from);
+            v = shfl_xyz(v, from);
+            idx = __shfl_sync(FULL, idx, from);
+            const unsigned khi = mine ? (unsigned)(kq >> 32) : 0xfffffffeu;
+            // ---- emit the children ----
+            const unsigned same = __match_any_sync(FULL, khi);
+            const bool start = mine && khi != 0xffffffffu && (__ffs(same) - 1) == lane;
+            const unsigned starts = __ballot_sync(FULL, start);
+            const int nch = __popc(starts);
+            if (sp + nch > TINY_STACK) {
+                if (lane == 0) dev_fail(st, DEV_OVERFLOW, 46, node);
+                break;
+            }
+            int id = -1;
+            if (start) {
+                id = atomicAdd(nd.counter, 1);
+                if (id >= nd.cap) {  // the host retries with a larger capacity
+                    dev_fail(st, DEV_OVERFLOW, 47, id);
+                    id = -1;
+                } else {
+                    nd.parent[id] = node;
+                    nd.level[id] = lev + 1;
+                    nd.first[id] = base + lane;
+                    nd.count[id] = __popc(same);
+                    nd.minidx[id] = (int)khi;
+                    nd.nchild[id] = 0;
+                    nd.tie[id] = 0;
+                    nd.root[id] = nd.root[node];
+                    nd.shift[id] = nd.shift[node];
+                }
+            }
+            const unsigned pushed = __ballot_sync(FULL, id >= 0);
+            if (id >= 0) stk[sp + __popc(pushed & ((1u << lane) - 1u))] = make_int4(lane, __popc(same), id, lev + 1);
+            sp += __popc(pushed);
+            if (lane == 0) {
+                nd.nchild[node] = __popc(pushed);
+                nd.tie[node] = tie;
+            }
+            __syncwarp();
+        }
+        if (lane < n0) widx[base + lane] = idx;
+        __syncwarp();
     }
 }
 
@@ -1761,9 +2024,10 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
     int *shift_bits = gmisc, *gmin = gmisc + G, *slot_group = gmisc + 2 * G;
     // node queues: big lists (ping-pong) and the small queue; counters
     // counters first (16 ints = 64 bytes, so everything after stays 8-byte aligned)
-    RS_WS(ctx, int, q, WS_RF_NODEQ, 3 * cap + 16);
-    int *ctr = q, *big_a = q + 16, *big_b = q + 16 + cap, *small_q = q + 16 + 2 * cap;
-    // ctr: [0] big_a len, [1] big_b len, [2] small len, [3] small head, [4] band len
+    RS_WS(ctx, int, q, WS_RF_NODEQ, 4 * cap + 16);
+    int *ctr = q, *big_a = q + 16, *big_b = q + 16 + cap, *small_q = q + 16 + 2 * cap, *tiny_q = q + 16 + 3 * cap;
+    // ctr: [0] big_a len, [1] big_b len, [2] small len, [3] small head, [4] band len,
+    // [6..7] bracket fallback flag, [8] tiny len, [9] tiny head
     RS_CUDA(ctx, cudaMemsetAsync(ctr, 0, sizeof(int) * 16, ctx->stream));
 
     const int gb = (int)std::min<int64_t>(G, (int64_t)ctx->num_sms * 8);
@@ -1982,7 +2246,10 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
     const size_t smem = sizeof(SmallShared);
     RS_CUDA(ctx, cudaFuncSetAttribute(k_small_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RS_LAUNCH(ctx, "rf_small_subtree", k_small_subtree, (int64_t)ctx->num_sms * 2, SMALL_THREADS, smem,
-              (const int *)small_q, (const int *)(ctr + 2), ctr + 3, (const float4 *)wpos, (const float4 *)wvel, widx,
+              (const int *)small_q, (const int *)(ctr + 2), ctr + 3, wpos, wvel, widx, tiny_q, ctr + 8, nd, box, f,
+              (int)min_n, ctx->d_status);
+    RS_LAUNCH(ctx, "rf_tiny_subtree", k_tiny_subtree, (int64_t)ctx->num_sms * 8, TINY_WARPS * 32, 0,
+              (const int *)tiny_q, (const int *)(ctr + 8), ctr + 9, (const float4 *)wpos, (const float4 *)wvel, widx,
               nd, box, f, (int)min_n, ctx->d_status);
 
     // ---- summary ----

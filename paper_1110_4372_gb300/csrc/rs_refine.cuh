@@ -193,8 +193,16 @@ struct MomOut {
     double xbar[3], vbar[3], sigx, sigv;
 };
 
+// x wrapped into [0, box).  Inside (-box, 2 box) one add or subtract gives
+// what fmod would (x - box is exact there, Sterbenz); fmod takes the rest.
 __device__ __forceinline__ double wrap_box(double x, double box)
 {
+    if (x >= 0 && x < box) return x;
+    if (x < 0 && x > -box) {
+        x += box;
+        return x >= box ? x - box : x;
+    }
+    if (x >= box && x < 2 * box) return x - box;
     x = fmod(x, box);
     if (x < 0) x += box;
     if (x >= box) x -= box;
@@ -207,12 +215,13 @@ __device__ __forceinline__ double wrap_box(double x, double box)
 __device__ __forceinline__ MomOut mom_finalize(const MomAcc &a, float4 pref, float4 vref, int64_t n, double box)
 {
     MomOut o;
-    const double nd = (double)n;
+    // float64 is scarce on this part: one reciprocal of n, the rest multiplies
+    const double inv_n = 1.0 / (double)n;
     const double ref[6] = {pref.x, pref.y, pref.z, vref.x, vref.y, vref.z};
     double s2x = 0, s2v = 0, mean[6];
     for (int i = 0; i < 6; i++) {
         double s = s128_to_double(a.s_lo[i], a.s_hi[i]) * RS_FX_INV;
-        mean[i] = s / nd;
+        mean[i] = s * inv_n;
         if (i < 3) s2x += s * s;
         else s2v += s * s;
     }
@@ -223,7 +232,7 @@ __device__ __forceinline__ MomOut mom_finalize(const MomAcc &a, float4 pref, flo
     const double q2 = RS_FX_INV * RS_FX_INV;
     double qx = u128_to_double(a.qx_lo, a.qx_hi) * q2;
     double qv = u128_to_double(a.qv_lo, a.qv_hi) * q2;
-    double vx = (qx - s2x / nd) / nd, vv = (qv - s2v / nd) / nd;
+    double vx = (qx - s2x * inv_n) * inv_n, vv = (qv - s2v * inv_n) * inv_n;
     o.sigx = vx > 0 ? sqrt(vx) : 0.0;
     o.sigv = vv > 0 ? sqrt(vv) : 0.0;
     return o;
