@@ -28,7 +28,7 @@ namespace {
 
 constexpr int64_t STATIC_MAX_N = 65536;           // particles per call
 constexpr int64_t STATIC_MAX_CELLS = 1 << 20;     // coarse cells of the neighbour table
-constexpr int64_t STATIC_SORT_TILE = 4096;        // keys per radix-sort tile
+constexpr int64_t STATIC_SORT_TILE = RS_SORT_TILE;  // keys per radix-sort tile
 constexpr int64_t STATIC_SCAN_BYTES = 64 * 1024;
 
 // byte size of each region, rounded to 256 so every region stays aligned

@@ -133,6 +133,8 @@ __host__ __device__ static inline int64_t ceil_div(int64_t a, int64_t b) { retur
 // In-place exclusive prefix sum; *total (device, optional) receives the sum.
 rs_status rs_scan_u32(rs_ctx *ctx, uint32_t *data, int64_t n, uint32_t *total);
 rs_status rs_scan_i64(rs_ctx *ctx, int64_t *data, int64_t n, int64_t *total);
+// keys per radix-sort tile; the histogram workspace holds 256 counts per tile
+constexpr int64_t RS_SORT_TILE = 2048;
 // Stable LSD radix sort of (key, value) pairs on key bits [0, nbits).  The
 // caller provides both ping-pong buffers; *out_in_alt says whether the
 // sorted data ended in (k1, v1).

@@ -120,10 +120,12 @@ rs_status scan_top(rs_ctx *ctx, T *data, int64_t n, T *total)
 // ---------------------------------------------------------------------------
 constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;
-constexpr int SORT_THREADS = 256;
+constexpr int SORT_THREADS = 256;  // one thread per digit in the scatter's digit scan
 constexpr int SORT_WARPS = SORT_THREADS / 32;
-constexpr int SORT_ITEMS = 16;
+constexpr int SORT_ITEMS = 8;
 constexpr int64_t SORT_TILE = SORT_THREADS * SORT_ITEMS;
+static_assert(SORT_TILE == RS_SORT_TILE, "tile size shared with the fixed-scratch entry point");
+static_assert(SORT_THREADS == RADIX, "the scatter gives each digit one thread");
 
 template <typename K>
 __global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const K *keys, int64_t n, int shift, uint32_t *hist,
@@ -142,18 +144,25 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const K *keys, int64
     for (int d = threadIdx.x; d < RADIX; d += SORT_THREADS) hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
 }
 
+// One tile: stable ranks per warp (match_any), the tile's keys placed in
+// shared memory in digit order, then written out in that order, so the
+// items of one digit go to consecutive global slots (coalesced stores).
 template <typename K>
 __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const K *kin, K *kout, const uint32_t *vin,
                                                                  uint32_t *vout, int64_t n, int shift,
                                                                  const uint32_t *hist, int64_t ntiles)
 {
     __shared__ uint32_t wcnt[SORT_WARPS][RADIX];
-    __shared__ uint32_t goff[RADIX];
+    __shared__ uint32_t goff[RADIX];    // first global slot of each digit for this tile
+    __shared__ uint32_t lstart[RADIX];  // first tile slot of each digit
+    __shared__ uint32_t wsum[SORT_WARPS];
+    __shared__ K skey[SORT_TILE];
+    __shared__ uint32_t sval[SORT_TILE];
     const int lane = lane_id(), w = warp_id();
     for (int d = lane; d < RADIX; d += 32) wcnt[w][d] = 0;
-    for (int d = threadIdx.x; d < RADIX; d += SORT_THREADS) goff[d] = hist[(int64_t)d * ntiles + blockIdx.x];
     __syncwarp();
-    const int64_t wbase = (int64_t)blockIdx.x * SORT_TILE + (int64_t)w * 32 * SORT_ITEMS;
+    const int64_t tbase = (int64_t)blockIdx.x * SORT_TILE;
+    const int64_t wbase = tbase + (int64_t)w * 32 * SORT_ITEMS;
     const uint32_t lt = (1u << lane) - 1u;
     K key[SORT_ITEMS];
     uint32_t val[SORT_ITEMS];
@@ -174,26 +183,48 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const K *kin, K *
         rank[j] = before + __popc(peers & lt);
     }
     __syncthreads();
-    // exclusive offsets of each warp within each digit
-    for (int d = threadIdx.x; d < RADIX; d += SORT_THREADS) {
-        uint32_t s = goff[d];
+    // thread d: offsets of each warp within digit d, then the tile-local start
+    // of digit d (an exclusive scan of the digit totals over the block)
+    {
+        const int d = threadIdx.x;
+        uint32_t tot = 0;
 #pragma unroll
         for (int ww = 0; ww < SORT_WARPS; ww++) {
-            uint32_t t = wcnt[ww][d];
-            wcnt[ww][d] = s;
-            s += t;
+            const uint32_t t = wcnt[ww][d];
+            wcnt[ww][d] = tot;
+            tot += t;
         }
+        uint32_t x = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        goff[d] = hist[(int64_t)d * ntiles + blockIdx.x];
+        __syncthreads();
+        uint32_t pre = 0;
+        for (int ww = 0; ww < w; ww++) pre += wsum[ww];
+        lstart[d] = pre + x - tot;
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < SORT_ITEMS; j++) {
-        int64_t i = wbase + j * 32 + lane;
-        if (i < n) {
-            uint32_t d = (uint32_t)(key[j] >> shift) & (RADIX - 1);
-            uint32_t pos = wcnt[w][d] + rank[j];
-            kout[pos] = key[j];
-            vout[pos] = val[j];
+        if (wbase + j * 32 + lane < n) {
+            const uint32_t d = (uint32_t)(key[j] >> shift) & (RADIX - 1);
+            const uint32_t lp = lstart[d] + wcnt[w][d] + rank[j];
+            skey[lp] = key[j];
+            sval[lp] = val[j];
         }
+    }
+    __syncthreads();
+    const int tn = (int)min((int64_t)SORT_TILE, n - tbase);
+    for (int i = threadIdx.x; i < tn; i += SORT_THREADS) {
+        const K k = skey[i];
+        const uint32_t d = (uint32_t)(k >> shift) & (RADIX - 1);
+        const uint32_t pos = goff[d] + ((uint32_t)i - lstart[d]);
+        kout[pos] = k;
+        vout[pos] = sval[i];
     }
 }
 
