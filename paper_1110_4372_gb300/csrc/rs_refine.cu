@@ -763,13 +763,15 @@ struct LevelBufs {
     int *tie;                // per rank
 };
 
-__global__ void k_lvl_prep(const int *list, int K, NodeArrays nd, int64_t *tiles, int64_t *segc)
+__global__ void k_lvl_prep(const int *list, int K, NodeArrays nd, int64_t *tiles, int64_t *segc,
+                           unsigned long long *max_count)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
     int c = nd.count[list[k]];
     tiles[k] = ceil_div(c, TQ);
     segc[k] = c;
+    atomicMax(max_count, (unsigned long long)c);
 }
 
 __global__ void k_lvl_tiles(int K, const int64_t *tile_off, int *tile_rank, int *tile_q0)
@@ -901,21 +903,15 @@ __device__ __forceinline__ MemberStore mem_shift(const MemberStore &M, int64_t b
 }
 
 // ---- per-node 32-ary bounding-volume hierarchy over the member range ----
-// Leaves hold BVH_LEAF = 32 consecutive members (the range is in 6D Morton
-// order); box (h, i) of level h is the union of boxes (h-1, 32i .. 32i+31),
-// so it spans members [i 32^(h+1), (i+1) 32^(h+1)).  The fan-out equals the
+// Leaves hold BVH_LEAF = 32 consecutive members (the range is in k-d order at
+// level 0, inherited below); box (h, i) of level h is the union of boxes
+// (h-1, 32i .. 32i+31), so it spans members [i 32^(h+1), (i+1) 32^(h+1)).  The fan-out equals the
 // warp width: a search gives each lane one child box of the box it opens, or
 // one member of the leaf it scans.  Boxes of a node are stored level by
 // level from its base offset.
 constexpr int BVH_LEAF = 32;
 constexpr int BVH_LOG = 5;  // log2 of the leaf size and of the fan-out
 constexpr int BVH_MAXH = 8;
-
-__device__ __forceinline__ int bvh_count(int nl, int h)
-{
-    for (int j = 0; j < h; j++) nl = (nl + 31) >> BVH_LOG;
-    return nl;
-}
 
 __device__ __forceinline__ int bvh_levels(int nl)
 {
@@ -1585,7 +1581,6 @@ __global__ void k_smp_thresh(LevelBufs L, NodeArrays nd, const int64_t *soff, co
     __shared__ float v[SMP_MAX];
     const int k = blockIdx.x;
     if (k >= L.K) return;
-    const int n = nd.count[L.list[k]];
     const int64_t a = soff[k];
     const int S = (int)(soff[k + 1] - a);
     for (int i = threadIdx.x; i < SMP_MAX; i += blockDim.x) v[i] = i < S ? sdnn[a + i] : INFINITY;
@@ -1632,37 +1627,88 @@ __global__ void k_bracket_check(LevelBufs L, const float *R2, const float *STOP,
     if (!((double)t32 * (1.0 - 4.0 * RS_BAND) >= (double)STOP[k])) atomicExch(fallback, 1);
 }
 
-// ---- level-0 ordering along a 6D Morton curve (locality for the boxes) ----
-__device__ __forceinline__ unsigned long long morton6(const unsigned c[6])
+// ---- level-0 ordering: k-d splits at leaf-aligned medians ----
+// A node's member range is split recursively: a range of m > 32 members
+// splits at h = m/2 rounded up to a multiple of 32, the h members with the
+// smallest coordinate on the round's axis going left, the axes cycling
+// through x, vx, y, vy, z, vz.  Every split lands on a leaf boundary, so each
+// leaf of 32 consecutive members is one cell of the k-d tree: compact in
+// phase space, which is what the leaf boxes of the searches need.  The split
+// positions depend only on the node's size, so each round is one stable sort
+// of all members by (segment, 16-bit coordinate), the coordinate relative to
+// the node's reference member in units of its dispersion.
+__host__ __device__ __forceinline__ int kd_split(int m)
 {
-    unsigned long long key = 0;
-    for (int bit = 6; bit >= 0; bit--)
-        for (int d = 0; d < 6; d++) key = (key << 1) | ((c[d] >> bit) & 1u);
-    return key;
+    int h = ((m / 2 + 31) / 32) * 32;
+    h = h < 32 ? 32 : h;
+    return h > m - 1 ? m - 1 : h;
 }
 
-__global__ void k_lvl_morton(LevelBufs L, NodeArrays nd, const float4 *wpos, const float4 *wvel,
-                             unsigned long long *keys, unsigned *vals)
+__host__ __device__ __forceinline__ int kd_rounds(int64_t m)
+{
+    int r = 0;
+    while (m > 32) {
+        m = kd_split((int)m);
+        r++;
+    }
+    return r;
+}
+
+__global__ void k_kd_keys(LevelBufs L, NodeArrays nd, const int64_t *seg_base, const float4 *wpos,
+                          const float4 *wvel, const unsigned *vin, unsigned long long *kout, unsigned *vout,
+                          int round)
 {
     const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x];
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
-    const int q = q0 + threadIdx.x;
-    if (q >= n) return;
-    const float4 pr = L.ref[2 * k], vr = L.ref[2 * k + 1];
-    const float ix = nd.sigx[node] > 0 ? (float)(1.0 / nd.sigx[node]) : 0.f;
-    const float iv = nd.sigv[node] > 0 ? (float)(1.0 / nd.sigv[node]) : 0.f;
-    const float4 p = wpos[first + q], v = wvel[first + q];
-    const float u[6] = {(p.x - pr.x) * ix, (p.y - pr.y) * ix, (p.z - pr.z) * ix,
-                        (v.x - vr.x) * iv, (v.y - vr.y) * iv, (v.z - vr.z) * iv};
-    unsigned c[6];
-    for (int d = 0; d < 6; d++) {
-        float t = (u[d] + 6.f) * (128.f / 12.f);
-        t = fminf(fmaxf(t, 0.f), 127.f);
-        c[d] = (unsigned)t;
+    const int p = q0 + threadIdx.x;
+    if (p >= n) return;
+    const int64_t P = L.seg_off[k] + p;
+    const unsigned slot = round == 0 ? (unsigned)(first + p) : vin[P];
+    int start = 0, size = n;
+    for (int i = 0; i < round && size > 32; i++) {
+        const int h = kd_split(size);
+        if (p - start < h) {
+            size = h;
+        } else {
+            start += h;
+            size -= h;
+        }
     }
-    const int64_t pidx = L.seg_off[k] + q;
-    keys[pidx] = ((unsigned long long)k << 42) | morton6(c);
-    vals[pidx] = (unsigned)(first + q);
+    const int axis = round % 6;  // x, vx, y, vy, z, vz
+    const int d = axis >> 1;
+    float c, r, inv;
+    if ((axis & 1) == 0) {
+        const float4 a = wpos[slot], ra = L.ref[2 * k];
+        c = d == 0 ? a.x : (d == 1 ? a.y : a.z);
+        r = d == 0 ? ra.x : (d == 1 ? ra.y : ra.z);
+        inv = nd.sigx[node] > 0 ? (float)(1.0 / nd.sigx[node]) : 0.f;
+    } else {
+        const float4 a = wvel[slot], ra = L.ref[2 * k + 1];
+        c = d == 0 ? a.x : (d == 1 ? a.y : a.z);
+        r = d == 0 ? ra.x : (d == 1 ? ra.y : ra.z);
+        inv = nd.sigv[node] > 0 ? (float)(1.0 / nd.sigv[node]) : 0.f;
+    }
+    const float u = ((c - r) * inv + 12.f) * (65536.f / 24.f);
+    const unsigned qv = (unsigned)fminf(fmaxf(u, 0.f), 65535.f);
+    kout[P] = ((unsigned long long)(seg_base[k] + start / 32) << 16) | qv;
+    vout[P] = slot;
+}
+
+// members into the sorted order of their node's range
+__global__ void k_kd_place(LevelBufs L, NodeArrays nd, const unsigned *vals, const float4 *wpos, const float4 *wvel,
+                           const int *widx, float4 *wpos2, float4 *wvel2, int *widx2, unsigned *dest)
+{
+    const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x];
+    const int node = L.list[k], first = nd.first[node], n = nd.count[node];
+    const int p = q0 + threadIdx.x;
+    if (p >= n) return;
+    const int64_t P = L.seg_off[k] + p;
+    const unsigned s = vals[P];
+    const int dd = first + p;
+    wpos2[dd] = wpos[s];
+    wvel2[dd] = wvel[s];
+    widx2[dd] = widx[s];
+    dest[P] = (unsigned)dd;
 }
 
 // radix select: pass 0 digits bits 31..21, pass 1 bits 20..10, pass 2 bits 9..0
@@ -2051,8 +2097,9 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         if (K == 0) break;
         RS_WS(ctx, int64_t, lv64, WS_RF_MISC1, 4 * (K + 1) + 8);
         int64_t *tiles = lv64, *segc = lv64 + (K + 1), *tot = lv64 + 2 * (K + 1);
+        RS_CUDA(ctx, cudaMemsetAsync(tot + 3, 0, sizeof(int64_t), ctx->stream));
         RS_LAUNCH(ctx, "rf_lvl_prep", k_lvl_prep, ceil_div(K, 256), 256, 0, (const int *)cur, (int)K, nd, tiles,
-                  segc);
+                  segc, (unsigned long long *)(tot + 3));
         RS_CUDA(ctx, cudaMemsetAsync(tiles + K, 0, sizeof(int64_t), ctx->stream));
         RS_CUDA(ctx, cudaMemsetAsync(segc + K, 0, sizeof(int64_t), ctx->stream));
         RS_TRY(rs_scan_i64(ctx, tiles, K + 1, tot));
@@ -2101,19 +2148,37 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         int rbits = 0;
         while (rbits < 32 && ((uint64_t)(K - 1) >> rbits) != 0) rbits++;
         if (level == 0) {
-            // order each big root's members along a 6D Morton curve; children
-            // keep this order through the stable child partition below
-            RS_LAUNCH(ctx, "rf_lvl_morton", k_lvl_morton, T, TQ, 0, L, nd, (const float4 *)wpos,
-                      (const float4 *)wvel, (unsigned long long *)k0, v0);
-            bool malt = false;
-            RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, LM, 42 + rbits, &malt));
-            const unsigned long long *mk = (const unsigned long long *)(malt ? k1 : k0);
-            const unsigned *mv = malt ? v1 : v0;
-            unsigned *mdest = (unsigned *)(malt ? v0 : v1);
-            RS_LAUNCH(ctx, "rf_lvl_scatter", k_lvl_scatter, ceil_div(LM, 256), 256, 0, L, nd, LM, mk, mv,
-                      (const float4 *)wpos, (const float4 *)wvel, (const int *)widx, wpos2, wvel2, widx2, mdest, 42);
-            RS_LAUNCH(ctx, "rf_lvl_copyback", k_lvl_copyback, ceil_div(LM, 256), 256, 0, LM, (const unsigned *)mdest,
-                      (const float4 *)wpos2, (const float4 *)wvel2, (const int *)widx2, wpos, wvel, widx);
+            // order each big root's members by k-d splits at leaf-aligned
+            // medians; children keep this order through the stable child
+            // partition below
+            int64_t maxn = 0;
+            RS_TRY(rs_read_i64(ctx, tot + 3, 1, &maxn, "rs_refine6d"));
+            RS_WS(ctx, int64_t, kw, WS_RF_MISC5, 2 * (K + 1) + 8);
+            int64_t *kseg = kw, *ktot = kw + (K + 1);
+            RS_LAUNCH(ctx, "rf_full_prep", k_full_prep, ceil_div(K, 256), 256, 0, (const int *)cur, (int)K, nd, kseg);
+            RS_CUDA(ctx, cudaMemsetAsync(kseg + K, 0, sizeof(int64_t), ctx->stream));
+            RS_TRY(rs_scan_i64(ctx, kseg, K + 1, ktot));
+            int64_t NS;
+            RS_TRY(rs_read_i64(ctx, ktot, 1, &NS, "rs_refine6d"));
+            int sbits = 0;
+            while (sbits < 40 && (NS >> sbits) != 0) sbits++;
+            const int R = kd_rounds(maxn);
+            const unsigned *vsorted = nullptr;
+            for (int r = 0; r < R; r++) {
+                RS_LAUNCH(ctx, "rf_kd_keys", k_kd_keys, T, TQ, 0, L, nd, (const int64_t *)kseg, (const float4 *)wpos,
+                          (const float4 *)wvel, vsorted, (unsigned long long *)k0, v0, r);
+                bool kalt = false;
+                RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, LM, 16 + sbits, &kalt));
+                vsorted = kalt ? v1 : v0;
+            }
+            if (R > 0) {
+                unsigned *kdest = (unsigned *)(vsorted == v0 ? v1 : v0);
+                RS_LAUNCH(ctx, "rf_kd_place", k_kd_place, T, TQ, 0, L, nd, vsorted, (const float4 *)wpos,
+                          (const float4 *)wvel, (const int *)widx, wpos2, wvel2, widx2, kdest);
+                RS_LAUNCH(ctx, "rf_lvl_copyback", k_lvl_copyback, ceil_div(LM, 256), 256, 0, LM,
+                          (const unsigned *)kdest, (const float4 *)wpos2, (const float4 *)wvel2, (const int *)widx2,
+                          wpos, wvel, widx);
+            }
         }
         // bounding-volume hierarchy of every big node
         RS_WS(ctx, int64_t, bo, WS_RF_MISC3, (K + 1) + 8);
