@@ -1644,16 +1644,43 @@ __host__ __device__ __forceinline__ int kd_split(int m)
     return h > m - 1 ? m - 1 : h;
 }
 
-__host__ __device__ __forceinline__ int kd_rounds(int64_t m)
+// splits until a range of m members is at most `limit`
+__host__ __device__ __forceinline__ int kd_rounds(int64_t m, int limit)
 {
     int r = 0;
-    while (m > 32) {
+    while (m > limit) {
         m = kd_split((int)m);
         r++;
     }
     return r;
 }
 
+constexpr int KD_CTA = 1024;  // ranges of at most this many members finish in one CTA
+
+// 16-bit coordinate of a member on an axis (x, vx, y, vy, z, vz), relative to
+// the node's reference member in units of its dispersion
+__device__ __forceinline__ unsigned kd_coord(const float4 *wpos, const float4 *wvel, unsigned slot, int axis,
+                                             float4 pref, float4 vref, float ix, float iv)
+{
+    const int d = axis >> 1;
+    float c, r, inv;
+    if ((axis & 1) == 0) {
+        const float4 a = wpos[slot];
+        c = d == 0 ? a.x : (d == 1 ? a.y : a.z);
+        r = d == 0 ? pref.x : (d == 1 ? pref.y : pref.z);
+        inv = ix;
+    } else {
+        const float4 a = wvel[slot];
+        c = d == 0 ? a.x : (d == 1 ? a.y : a.z);
+        r = d == 0 ? vref.x : (d == 1 ? vref.y : vref.z);
+        inv = iv;
+    }
+    const float u = ((c - r) * inv + 12.f) * (65536.f / 24.f);
+    return (unsigned)fminf(fmaxf(u, 0.f), 65535.f);
+}
+
+// One global round: ranges of more than KD_CTA members at this depth are
+// sorted by the round's axis; smaller ranges keep their order (value 0).
 __global__ void k_kd_keys(LevelBufs L, NodeArrays nd, const int64_t *seg_base, const float4 *wpos,
                           const float4 *wvel, const unsigned *vin, unsigned long long *kout, unsigned *vout,
                           int round)
@@ -1665,7 +1692,7 @@ __global__ void k_kd_keys(LevelBufs L, NodeArrays nd, const int64_t *seg_base, c
     const int64_t P = L.seg_off[k] + p;
     const unsigned slot = round == 0 ? (unsigned)(first + p) : vin[P];
     int start = 0, size = n;
-    for (int i = 0; i < round && size > 32; i++) {
+    for (int i = 0; i < round && size > KD_CTA; i++) {
         const int h = kd_split(size);
         if (p - start < h) {
             size = h;
@@ -1674,24 +1701,127 @@ __global__ void k_kd_keys(LevelBufs L, NodeArrays nd, const int64_t *seg_base, c
             size -= h;
         }
     }
-    const int axis = round % 6;  // x, vx, y, vy, z, vz
-    const int d = axis >> 1;
-    float c, r, inv;
-    if ((axis & 1) == 0) {
-        const float4 a = wpos[slot], ra = L.ref[2 * k];
-        c = d == 0 ? a.x : (d == 1 ? a.y : a.z);
-        r = d == 0 ? ra.x : (d == 1 ? ra.y : ra.z);
-        inv = nd.sigx[node] > 0 ? (float)(1.0 / nd.sigx[node]) : 0.f;
-    } else {
-        const float4 a = wvel[slot], ra = L.ref[2 * k + 1];
-        c = d == 0 ? a.x : (d == 1 ? a.y : a.z);
-        r = d == 0 ? ra.x : (d == 1 ? ra.y : ra.z);
-        inv = nd.sigv[node] > 0 ? (float)(1.0 / nd.sigv[node]) : 0.f;
+    unsigned qv = 0;
+    if (size > KD_CTA) {
+        const float ix = nd.sigx[node] > 0 ? (float)(1.0 / nd.sigx[node]) : 0.f;
+        const float iv = nd.sigv[node] > 0 ? (float)(1.0 / nd.sigv[node]) : 0.f;
+        qv = kd_coord(wpos, wvel, slot, round % 6, L.ref[2 * k], L.ref[2 * k + 1], ix, iv);
     }
-    const float u = ((c - r) * inv + 12.f) * (65536.f / 24.f);
-    const unsigned qv = (unsigned)fminf(fmaxf(u, 0.f), 65535.f);
     kout[P] = ((unsigned long long)(seg_base[k] + start / 32) << 16) | qv;
     vout[P] = slot;
+}
+
+// Ranges of at most KD_CTA members left by the global rounds, one entry per
+// range: (rank, start in the node, size, depth).  One thread per node.
+__global__ void k_kd_ranges(LevelBufs L, NodeArrays nd, int4 *ranges, int *count, int cap, rs_dev_status *st)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.K) return;
+    const int n = nd.count[L.list[k]];
+    int stk_s[32], stk_m[32], stk_d[32];
+    int sp = 0;
+    stk_s[0] = 0;
+    stk_m[0] = n;
+    stk_d[0] = 0;
+    sp = 1;
+    for (int it = 0; sp > 0 && it < (1 << 26); it++) {
+        sp--;
+        const int s0 = stk_s[sp], m = stk_m[sp], d = stk_d[sp];
+        if (m <= KD_CTA) {
+            if (m > 32) {
+                const int slot = atomicAdd(count, 1);
+                if (slot < cap) ranges[slot] = make_int4(k, s0, m, d);
+                else dev_fail(st, DEV_OVERFLOW, 58, slot);
+            }
+            continue;
+        }
+        if (sp + 2 > 32) {
+            dev_fail(st, DEV_OVERFLOW, 59, k);
+            return;
+        }
+        const int h = kd_split(m);
+        stk_s[sp] = s0 + h;
+        stk_m[sp] = m - h;
+        stk_d[sp++] = d + 1;
+        stk_s[sp] = s0;
+        stk_m[sp] = h;
+        stk_d[sp++] = d + 1;
+    }
+}
+
+// Finish one range in shared memory: the remaining splits, each round a
+// bitonic sort of (sub-range, coordinate, element) keys.
+__global__ void __launch_bounds__(256) k_kd_finish(LevelBufs L, NodeArrays nd, const int4 *ranges, const int *count,
+                                                     const float4 *wpos, const float4 *wvel, unsigned *vals)
+{
+    __shared__ unsigned short q[6][KD_CTA];
+    __shared__ unsigned slot[KD_CTA];
+    __shared__ unsigned long long key[KD_CTA];
+    __shared__ unsigned short perm[KD_CTA];
+    const int nr = *count;
+    for (int ri = blockIdx.x; ri < nr; ri += gridDim.x) {
+        const int4 rg = ranges[ri];
+        const int k = rg.x, s0 = rg.y, m = rg.z, d0 = rg.w;
+        const int node = L.list[k];
+        const int64_t P0 = L.seg_off[k] + s0;
+        const float ix = nd.sigx[node] > 0 ? (float)(1.0 / nd.sigx[node]) : 0.f;
+        const float iv = nd.sigv[node] > 0 ? (float)(1.0 / nd.sigv[node]) : 0.f;
+        const float4 pref = L.ref[2 * k], vref = L.ref[2 * k + 1];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const unsigned sl = vals[P0 + i];
+            slot[i] = sl;
+            for (int a = 0; a < 6; a++) q[a][i] = (unsigned short)kd_coord(wpos, wvel, sl, a, pref, vref, ix, iv);
+            perm[i] = (unsigned short)i;
+        }
+        int P2 = 1;
+        while (P2 < m) P2 <<= 1;
+        const int R = kd_rounds(m, 32);
+        __syncthreads();
+        for (int r = 0; r < R; r++) {
+            const int axis = (d0 + r) % 6;
+            for (int j = threadIdx.x; j < P2; j += blockDim.x) {
+                unsigned long long kk = ~0ull;
+                if (j < m) {
+                    int start = 0, size = m;
+                    for (int i = 0; i < r && size > 32; i++) {
+                        const int h = kd_split(size);
+                        if (j - start < h) {
+                            size = h;
+                        } else {
+                            start += h;
+                            size -= h;
+                        }
+                    }
+                    const unsigned e = perm[j];
+                    const unsigned v = size > 32 ? q[axis][e] : 0u;
+                    kk = ((unsigned long long)(start / 32) << 40) | ((unsigned long long)v << 16) | j;
+                }
+                key[j] = kk;
+            }
+            __syncthreads();
+            for (int kb = 2; kb <= P2; kb <<= 1)
+                for (int jb = kb >> 1; jb > 0; jb >>= 1) {
+                    for (int t = threadIdx.x; t < P2 / 2; t += blockDim.x) {
+                        const int i = 2 * jb * (t / jb) + (t % jb), l = i + jb;
+                        const bool up = (i & kb) == 0;
+                        const unsigned long long x = key[i], y = key[l];
+                        if ((x > y) == up) {
+                            key[i] = y;
+                            key[l] = x;
+                        }
+                    }
+                    __syncthreads();
+                }
+            // new order: position j holds the element that was at position key & 0xffff
+            unsigned short np[KD_CTA / 256];
+            for (int j = threadIdx.x, c = 0; j < m; j += blockDim.x, c++) np[c] = perm[(int)(key[j] & 0xffffu)];
+            __syncthreads();
+            for (int j = threadIdx.x, c = 0; j < m; j += blockDim.x, c++) perm[j] = np[c];
+            __syncthreads();
+        }
+        for (int j = threadIdx.x; j < m; j += blockDim.x) vals[P0 + j] = slot[perm[j]];
+        __syncthreads();
+    }
 }
 
 // members into the sorted order of their node's range
@@ -2162,7 +2292,7 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
             RS_TRY(rs_read_i64(ctx, ktot, 1, &NS, "rs_refine6d"));
             int sbits = 0;
             while (sbits < 40 && (NS >> sbits) != 0) sbits++;
-            const int R = kd_rounds(maxn);
+            const int R = kd_rounds(maxn, KD_CTA);
             const unsigned *vsorted = nullptr;
             for (int r = 0; r < R; r++) {
                 RS_LAUNCH(ctx, "rf_kd_keys", k_kd_keys, T, TQ, 0, L, nd, (const int64_t *)kseg, (const float4 *)wpos,
@@ -2171,7 +2301,21 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
                 RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, LM, 16 + sbits, &kalt));
                 vsorted = kalt ? v1 : v0;
             }
-            if (R > 0) {
+            // ranges of at most KD_CTA members finish in one CTA each
+            const int64_t rcap = ceil_div(LM, 32) + K;
+            RS_WS(ctx, int4, kranges, WS_RF_JOBS, rcap + 1);
+            int *kcount = ctr + 10;
+            RS_CUDA(ctx, cudaMemsetAsync(kcount, 0, sizeof(int), ctx->stream));
+            RS_LAUNCH(ctx, "rf_kd_ranges", k_kd_ranges, ceil_div(K, 128), 128, 0, L, nd, kranges, kcount, (int)rcap,
+                      ctx->d_status);
+            if (R == 0)  // every member in its own position: round 0 writes the slots
+                RS_LAUNCH(ctx, "rf_kd_keys", k_kd_keys, T, TQ, 0, L, nd, (const int64_t *)kseg,
+                          (const float4 *)wpos, (const float4 *)wvel, vsorted, (unsigned long long *)k0, v0, 0);
+            unsigned *vfin = R > 0 ? (unsigned *)vsorted : v0;
+            RS_LAUNCH(ctx, "rf_kd_finish", k_kd_finish, (int64_t)ctx->num_sms * 8, 256, 0, L, nd,
+                      (const int4 *)kranges, (const int *)kcount, (const float4 *)wpos, (const float4 *)wvel, vfin);
+            vsorted = vfin;
+            {
                 unsigned *kdest = (unsigned *)(vsorted == v0 ? v1 : v0);
                 RS_LAUNCH(ctx, "rf_kd_place", k_kd_place, T, TQ, 0, L, nd, vsorted, (const float4 *)wpos,
                           (const float4 *)wvel, (const int *)widx, wpos2, wvel2, widx2, kdest);
