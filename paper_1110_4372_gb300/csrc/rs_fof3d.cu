@@ -196,67 +196,129 @@ __device__ __forceinline__ int pair_link(const float4 &pa, const float4 &pb, int
     return e2 <= g.l2 ? 1 : 0;
 }
 
-// One thread per fine cell: join it with every fine cell of larger index
-// within two fine cells per axis that has a friend pair with it.  Pass 0
-// takes the 26 adjacent cells (offsets of at most 1 per axis), where pairs are
-// friends almost at once in dense regions; pass 1 takes the cells two apart
-// on some axis, by which time dense regions are mostly one set and the
-// same-set check skips them.  Coarse cells numbered below the query's hold
-// only fine cells of smaller index and are not visited.
+// position of the j-th (0-based) set bit of a 64-bit mask with at least j + 1 bits
+__device__ __forceinline__ int nth_bit64(uint64_t m, int j)
+{
+    const unsigned lo = (unsigned)m, hi = (unsigned)(m >> 32);
+    const int nlo = __popc(lo);
+    return j < nlo ? (int)__fns(lo, 0, j + 1) : 32 + (int)__fns(hi, 0, j - nlo + 1);
+}
+
+// Join fine cell A with every fine cell of larger index within two fine cells
+// per axis that has a friend pair with it.  Pass 0 takes the 26 adjacent
+// cells (offsets of at most 1 per axis), where pairs are friends almost at
+// once in dense regions; pass 1 takes the cells two apart on some axis, by
+// which time dense regions are mostly one set and the same-set check skips
+// them.  Coarse cells numbered below A's hold only fine cells of smaller
+// index and are not visited.
+//
+// A warp takes 32 consecutive fine cells, a lane each.  For each of the
+// eight coarse cells around them every lane forms its mask of candidate fine
+// cells; the warp then numbers all lanes' candidates (a prefix sum of the
+// mask popcounts) and deals them out 32 at a time, so each lane tests one
+// candidate pair per round whatever the spread of candidates over the cells.
 __global__ void __launch_bounds__(FOF_THREADS) k_fof_link(const uint32_t *n_cells_p, const uint64_t *cell_key,
                                                             const uint32_t *cell_start, const uint32_t *table,
                                                             const uint64_t *occ, const float4 *spos, int *parent,
                                                             FofGeom g, int pass, rs_dev_status *st)
 {
+    const unsigned FULL = 0xffffffffu;
     const int64_t M = *n_cells_p;
-    for (int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; A < M; A += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t ka = cell_key[A], ca = ka >> 6;
-        const int sa = (int)(ka & 63), ux = sa & 3, uy = (sa >> 2) & 3, uz = sa >> 4;
-        int ccx, ccy, ccz;
-        coarse_coords(ca, g.Gc, ccx, ccy, ccz);
+    const int lane = lane_id();
+    const int64_t wfirst = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31));
+    for (int64_t wb = wfirst; wb < M; wb += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t A = wb + lane;
+        const bool va = A < M;
+        uint64_t ca = 0;
+        int sa = 0, ux = 0, uy = 0, uz = 0, ccx = 0, ccy = 0, ccz = 0;
+        uint32_t a0 = 0, a1 = 0;
+        if (va) {
+            const uint64_t ka = cell_key[A];
+            ca = ka >> 6;
+            sa = (int)(ka & 63);
+            ux = sa & 3;
+            uy = (sa >> 2) & 3;
+            uz = sa >> 4;
+            coarse_coords(ca, g.Gc, ccx, ccy, ccz);
+            a0 = cell_start[A];
+            a1 = cell_start[A + 1];
+        }
         const int ax = 4 * ccx + ux, ay = 4 * ccy + uy, az = 4 * ccz + uz;
-        const uint32_t a0 = cell_start[A], a1 = cell_start[A + 1];
         const int lox = ux < 2 ? -1 : 0, loy = uy < 2 ? -1 : 0, loz = uz < 2 ? -1 : 0;
-        for (int dz = loz; dz <= loz + 1; dz++) {
-            int cz = ccz + dz;
+        for (int s8 = 0; s8 < 8; s8++) {
+            const int dz = loz + (s8 >> 2), dy = loy + ((s8 >> 1) & 1), dx = lox + (s8 & 1);
+            int cz = ccz + dz, cy = ccy + dy, cx = ccx + dx;
             cz = cz < 0 ? cz + g.Gc : (cz >= g.Gc ? cz - g.Gc : cz);
-            for (int dy = loy; dy <= loy + 1; dy++) {
-                int cy = ccy + dy;
-                cy = cy < 0 ? cy + g.Gc : (cy >= g.Gc ? cy - g.Gc : cy);
-                for (int dx = lox; dx <= lox + 1; dx++) {
-                    int cx = ccx + dx;
-                    cx = cx < 0 ? cx + g.Gc : (cx >= g.Gc ? cx - g.Gc : cx);
-                    const uint64_t cc = ((uint64_t)cz * g.Gc + cy) * g.Gc + cx;
-                    if (cc < ca) continue;  // only fine cells of smaller index
-                    const uint32_t b0c = table[cc];
-                    if (b0c == 0xffffffffu) continue;
-                    const uint64_t om = occ[b0c];
-                    const uint64_t near = reach_mask(ux, uy, uz, dx, dy, dz, 1);
-                    uint64_t cand = om & (pass == 0 ? near : reach_mask(ux, uy, uz, dx, dy, dz, 2) & ~near);
-                    if (cc == ca) cand &= ~((2ull << sa) - 1ull);  // sub-cells after A's
-                    while (cand) {
-                        const int sb = __ffsll((long long)cand) - 1;
-                        cand &= cand - 1ull;
-                        const int64_t B = (int64_t)b0c + __popcll(om & ((1ull << sb) - 1ull));
-                        const int bx = 4 * cx + (sb & 3), by = 4 * cy + ((sb >> 2) & 3), bz = 4 * cz + (sb >> 4);
-                        int sx, sy, sz;
-                        fine_offset(ax, bx, g.Gf, sx);
-                        fine_offset(ay, by, g.Gf, sy);
-                        fine_offset(az, bz, g.Gf, sz);
-                        if (uf_find(parent, (int)A, st) == uf_find(parent, (int)B, st)) continue;
+            cy = cy < 0 ? cy + g.Gc : (cy >= g.Gc ? cy - g.Gc : cy);
+            cx = cx < 0 ? cx + g.Gc : (cx >= g.Gc ? cx - g.Gc : cx);
+            uint64_t cand = 0, om = 0;
+            uint32_t b0c = 0;
+            if (va) {
+                const uint64_t cc = ((uint64_t)cz * g.Gc + cy) * g.Gc + cx;
+                if (cc >= ca) {  // coarse cells below A's hold only fine cells of smaller index
+                    b0c = table[cc];
+                    if (b0c != 0xffffffffu) {
+                        om = occ[b0c];
+                        const uint64_t near = reach_mask(ux, uy, uz, dx, dy, dz, 1);
+                        cand = om & (pass == 0 ? near : reach_mask(ux, uy, uz, dx, dy, dz, 2) & ~near);
+                        if (cc == ca) cand &= ~((2ull << sa) - 1ull);  // sub-cells after A's
+                    }
+                }
+            }
+            for (int guard = 0; guard < 4096; guard++) {
+                const int cnt = __popcll(cand);
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int total = __shfl_sync(FULL, incl, 31);
+                if (total == 0) break;
+                const int excl = incl - cnt;
+                // this lane's candidate: number `lane` in the warp's order
+                int lo = 0, hi = 31;
+#pragma unroll
+                for (int it = 0; it < 5; it++) {
+                    const int mid = (lo + hi) >> 1;
+                    if (__shfl_sync(FULL, incl, mid) > lane) hi = mid;
+                    else lo = mid + 1;
+                }
+                const int src = lo;
+                const int j = lane - __shfl_sync(FULL, excl, src);
+                const uint64_t smask = __shfl_sync(FULL, cand, src), som = __shfl_sync(FULL, om, src);
+                const uint32_t sb0 = __shfl_sync(FULL, b0c, src), sa0 = __shfl_sync(FULL, a0, src),
+                               sa1 = __shfl_sync(FULL, a1, src);
+                const int sax = __shfl_sync(FULL, ax, src), say = __shfl_sync(FULL, ay, src),
+                          saz = __shfl_sync(FULL, az, src);
+                const int scx = __shfl_sync(FULL, cx, src), scy = __shfl_sync(FULL, cy, src),
+                          scz = __shfl_sync(FULL, cz, src);
+                const int sA = (int)(wb + src);
+                if (lane < total) {
+                    const int sb = nth_bit64(smask, j);
+                    const int B = (int)(sb0 + __popcll(som & ((1ull << sb) - 1ull)));
+                    const int bx = 4 * scx + (sb & 3), by = 4 * scy + ((sb >> 2) & 3), bz = 4 * scz + (sb >> 4);
+                    int sx, sy, sz;
+                    fine_offset(sax, bx, g.Gf, sx);
+                    fine_offset(say, by, g.Gf, sy);
+                    fine_offset(saz, bz, g.Gf, sz);
+                    if (uf_find(parent, sA, st) != uf_find(parent, B, st)) {
                         const uint32_t b0 = cell_start[B], b1 = cell_start[B + 1];
                         bool linked = false;
-                        for (uint32_t i = a0; i < a1 && !linked; i++) {
+                        for (uint32_t i = sa0; i < sa1 && !linked; i++) {
                             const float4 pa = spos[i];
-                            for (uint32_t j = b0; j < b1; j++)
-                                if (pair_link(pa, spos[j], sx, sy, sz, g)) {
+                            for (uint32_t q = b0; q < b1; q++)
+                                if (pair_link(pa, spos[q], sx, sy, sz, g)) {
                                     linked = true;
                                     break;
                                 }
                         }
-                        if (linked) uf_union(parent, (int)A, (int)B, st);
+                        if (linked) uf_union(parent, sA, B, st);
                     }
                 }
+                // drop the candidates dealt out this round (the lowest ones of each lane)
+                const int used = max(0, min(incl, 32) - excl);
+                for (int u = 0; u < used; u++) cand &= cand - 1ull;
             }
         }
     }
