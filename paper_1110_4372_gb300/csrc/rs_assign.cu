@@ -119,14 +119,47 @@ __device__ double merge_distance(const NodeArrays &nd, int a, int b, double box)
     return sqrt(f64_add(ratio2(dx2, f64_mul(mux, mux)), ratio2(dv2, f64_mul(muv, muv))));
 }
 
+// A float32 lower bound of the squared Eq. 2 separation: each coordinate gap
+// is shrunk by a bound on the rounding of the float32 copies (2^-22 of the
+// coordinates' size covers both roundings and the subtraction), and the
+// comparison keeps a 2^-10 relative margin for the float32 products and
+// sums.  Returns false when the pair may be within the threshold (or a
+// dispersion is zero): the float64 test then decides.
+__device__ __forceinline__ bool merge_far_f32(const NodeArrays &nd, int a, int b, float boxf, float thresh2)
+{
+    const int na = nd.count[a], nb = nd.count[b];
+    const bool a_small = (na != nb) ? (na < nb) : (nd.minidx[a] > nd.minidx[b]);
+    const int s = a_small ? a : b;
+    const float sx = (float)nd.sigx[s], sv = (float)nd.sigv[s];
+    if (!(sx > 1e-30f) || !(sv > 1e-30f)) return false;
+    float gx2 = 0.f, gv2 = 0.f;
+    for (int d = 0; d < 3; d++) {
+        const float xa = (float)nd.xbar[3 * a + d], xb = (float)nd.xbar[3 * b + d];
+        float dx = fabsf(xa - xb);
+        dx = fminf(dx, boxf - dx);
+        const float ex = 2.384185791015625e-07f * (fabsf(xa) + fabsf(xb) + boxf);
+        const float lx = fmaxf(0.f, dx - ex);
+        gx2 += lx * lx;
+        const float va = (float)nd.vbar[3 * a + d], vb = (float)nd.vbar[3 * b + d];
+        const float ev = 2.384185791015625e-07f * (fabsf(va) + fabsf(vb));
+        const float lv = fmaxf(0.f, fabsf(va - vb) - ev);
+        gv2 += lv * lv;
+    }
+    const float ns = (float)nd.count[s];
+    const float d2 = gx2 * ns / (sx * sx) + gv2 * ns / (sv * sv);
+    return d2 > thresh2 * 1.0009765625f;
+}
+
 __global__ void k_as_merge(AsBufs A, NodeArrays nd, double box, double thresh, rs_dev_status *st)
 {
+    const float boxf = (float)box, thresh2 = (float)(thresh * thresh);
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < A.L; a += gridDim.x * blockDim.x) {
         const int na = A.leaf_node[a];
         const int ra = nd.root[na];
         for (int b = a + 1; b < A.L; b++) {
             const int nb = A.leaf_node[b];
             if (nd.root[nb] != ra) break;
+            if (merge_far_f32(nd, na, nb, boxf, thresh2)) continue;
             if (merge_distance(nd, na, nb, box) < thresh) uf_union(A.uf, a, b, st);
         }
     }
@@ -428,61 +461,96 @@ __device__ __forceinline__ float as_d2_32(float4 p, float4 v, const float *f)
 // The node's seeds are the seed-list run [la, lb); their halos are
 // deduplicated in shared memory, then each member takes the only halo or the
 // Eq. 3 nearest one (float32 pass, float64 over the float32 band).
+// Seeds under each node: the first (la) and how many (nl).
+__global__ void k_as_nl(AsBufs A, NodeArrays nd, int nn, int *node_la, int64_t *nlv)
+{
+    const int node = blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= nn) return;
+    const int first = nd.first[node], cnt = nd.count[node];
+    const int la = lower_bound_u32(A.leaf_first, A.L, (unsigned)first);
+    const int lb = lower_bound_u32(A.leaf_first, A.L, (unsigned)(first + cnt));
+    node_la[node] = la;
+    nlv[node] = lb - la;
+}
+
+// The distinct candidate halos (roots of the seeds under a node), once per
+// node: the node's first tile sorts the seeds' roots in shared memory and
+// keeps the first of each run, into the node's own region cand_g[coff ..).
+// ncand[node] = the list's length, or -(seeds) - 1 when there are too many
+// seeds to stage, in which case the raw roots stand in (repeats only cost
+// time).
+__global__ void __launch_bounds__(AS_THREADS) k_as_cand(AsBufs A, NodeArrays nd, const int *leaf_root,
+                                                        const int *tnode, const int *tq0, const int *node_la,
+                                                        const int64_t *coff, int *cand_g, int *ncand)
+{
+    __shared__ int cand[AS_CAND];
+    __shared__ int wsum[AS_THREADS / 32];
+    if (tq0[blockIdx.x] != 0) return;
+    const int node = tnode[blockIdx.x];
+    const int la = node_la[node];
+    const int nl = (int)(coff[node + 1] - coff[node]);
+    int *out = cand_g + coff[node];
+    if (nl > AS_CAND || nl <= 0) {
+        if (threadIdx.x == 0) ncand[node] = -nl - 1;
+        return;
+    }
+    int P = 1;
+    while (P < nl) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += AS_THREADS) cand[i] = i < nl ? leaf_root[la + i] : 0x7fffffff;
+    __syncthreads();
+    for (int kk = 2; kk <= P; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < P / 2; t += AS_THREADS) {
+                int i = 2 * j * (t / j) + (t % j), l = i + j;
+                bool up = (i & kk) == 0;
+                int x = cand[i], y = cand[l];
+                if ((x > y) == up) {
+                    cand[i] = y;
+                    cand[l] = x;
+                }
+            }
+            __syncthreads();
+        }
+    // first of each run: a block-wide exclusive scan of the run-start flags
+    const int per = (nl + AS_THREADS - 1) / AS_THREADS;
+    const int i0 = threadIdx.x * per, i1 = min(nl, i0 + per);
+    int c = 0;
+    for (int i = i0; i < i1; i++) c += (i == 0 || cand[i] != cand[i - 1]) ? 1 : 0;
+    int x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane_id() >= o) x += y;
+    }
+    if (lane_id() == 31) wsum[warp_id()] = x;
+    __syncthreads();
+    int pre = 0;
+    for (int w = 0; w < warp_id(); w++) pre += wsum[w];
+    int o = pre + x - c;
+    for (int i = i0; i < i1; i++)
+        if (i == 0 || cand[i] != cand[i - 1]) out[o++] = cand[i];
+    if (threadIdx.x == AS_THREADS - 1) ncand[node] = pre + x;
+}
+
 __global__ void __launch_bounds__(AS_THREADS) k_as_assign(AsBufs A, NodeArrays nd, const int *leaf_root,
+                                                          const int *cand_g, const int *node_la, const int64_t *coff,
+                                                          const int *ncand,
                                                           const int *tnode, const int *tq0, const int *members,
                                                           const float *pos, const float *vel, int stride,
                                                           double box, float boxf, int32_t *halo_id,
                                                           rs_dev_status *st)
 {
-    __shared__ int cand[AS_CAND];
-    __shared__ int s_la, s_lb, s_nc;
     const int node = tnode[blockIdx.x];
     const int q0 = tq0[blockIdx.x];
     const int first = nd.first[node], cnt = nd.count[node];
     const int tail0 = first + A.span[node];
-    if (threadIdx.x == 0) {
-        s_la = lower_bound_u32(A.leaf_first, A.L, (unsigned)first);
-        s_lb = lower_bound_u32(A.leaf_first, A.L, (unsigned)(first + cnt));
-    }
-    __syncthreads();
-    const int la = s_la, lb = s_lb;
-    const int nl = lb - la;
-    const bool staged = nl <= AS_CAND;
-    int nc = nl;
-    const int *cl = leaf_root + la;  // candidate halo roots (possibly repeated)
-    if (staged) {
-        int P = 1;
-        while (P < nl) P <<= 1;
-        for (int i = threadIdx.x; i < P; i += AS_THREADS) cand[i] = i < nl ? leaf_root[la + i] : 0x7fffffff;
-        __syncthreads();
-        for (int kk = 2; kk <= P; kk <<= 1)
-            for (int j = kk >> 1; j > 0; j >>= 1) {
-                for (int t = threadIdx.x; t < P / 2; t += AS_THREADS) {
-                    int i = 2 * j * (t / j) + (t % j), l = i + j;
-                    bool up = (i & kk) == 0;
-                    int x = cand[i], y = cand[l];
-                    if ((x > y) == up) {
-                        cand[i] = y;
-                        cand[l] = x;
-                    }
-                }
-                __syncthreads();
-            }
-        // unique, in place, by one thread (nl <= 4096)
-        if (threadIdx.x == 0) {
-            int u = 0;
-            for (int i = 0; i < nl; i++)
-                if (i == 0 || cand[i] != cand[i - 1]) cand[u++] = cand[i];
-            s_nc = u;
-        }
-        __syncthreads();
-        nc = s_nc;
-        cl = cand;
-    }
+    const int la = node_la[node], nq = ncand[node];
+    // candidate halo roots: the distinct list, or the raw roots (with repeats)
+    const int nc = nq >= 0 ? nq : -nq - 1;
+    const int *cl = nq >= 0 ? cand_g + coff[node] : leaf_root + la;
     const int m = tail0 + q0 + threadIdx.x;
     if (m >= first + cnt) return;
     const int i = members[m];
-    if (nl <= 0) {
+    if (nc <= 0) {
         dev_fail(st, DEV_INTERNAL, 60, node);
         return;
     }
@@ -719,8 +787,20 @@ extern "C" rs_status rs_assign(rs_ctx *ctx, const rs_tree *t, const float *pos, 
     RS_WS(ctx, int, tt, WS_RF_MISC2, 2 * T + 8);
     RS_LAUNCH(ctx, "as_tiles_fill", k_as_tiles_fill, std::min<int64_t>(nn, 65535), 128, 0, nn, (const int64_t *)tl, tt,
               tt + T);
-    RS_LAUNCH(ctx, "as_assign", k_as_assign, T, AS_THREADS, 0, A, nd, (const int *)leaf_root, (const int *)tt,
-              (const int *)(tt + T),
+    // distinct candidate halos of every node, once per node
+    RS_WS(ctx, int64_t, cw, WS_AS_8, 2 * (int64_t)nn + 8);
+    int64_t *coff = cw;
+    int *node_la = (int *)(cw + nn + 4), *ncand = node_la + nn;
+    RS_LAUNCH(ctx, "as_nl", k_as_nl, ceil_div(nn, 256), 256, 0, A, nd, (int)nn, node_la, coff);
+    RS_CUDA(ctx, cudaMemsetAsync(coff + nn, 0, sizeof(int64_t), ctx->stream));
+    RS_TRY(rs_scan_i64(ctx, coff, nn + 1, coff + nn + 2));
+    int64_t CT;
+    RS_TRY(rs_read_i64(ctx, coff + nn, 1, &CT, "rs_assign"));
+    RS_WS(ctx, int, cand_g, WS_AS_9, CT + 8);
+    RS_LAUNCH(ctx, "as_cand", k_as_cand, T, AS_THREADS, 0, A, nd, (const int *)leaf_root, (const int *)tt,
+              (const int *)(tt + T), (const int *)node_la, (const int64_t *)coff, cand_g, ncand);
+    RS_LAUNCH(ctx, "as_assign", k_as_assign, T, AS_THREADS, 0, A, nd, (const int *)leaf_root, (const int *)cand_g,
+              (const int *)node_la, (const int64_t *)coff, (const int *)ncand, (const int *)tt, (const int *)(tt + T),
               (const int *)t->members, pos, vel, stride, box, boxf, halo_id, ctx->d_status);
     if (n_halos) {
         *n_halos = H;
