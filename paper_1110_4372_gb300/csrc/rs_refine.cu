@@ -1924,30 +1924,77 @@ __global__ void __launch_bounds__(TQ) k_lvl_band(LevelBufs L, NodeArrays nd, con
     }
 }
 
-__global__ void __launch_bounds__(TQ) k_lvl_band_exact(LevelBufs L, NodeArrays nd, const float4 *wpos,
-                                                       const float4 *wvel, const float *dnn)
+// Exact float64 nearest-neighbour distance of a band member: the minimum
+// float64 distance over the members whose float32 distance is within `lim`
+// (a bound above the member's float32 value), one warp per band member over
+// the node's hierarchy.  A box is skipped only when its float32 bound exceeds
+// lim by the pruning slack, so every member that passes the float32 test is
+// evaluated.
+__global__ void __launch_bounds__(W_WARPS * 32) k_lvl_band_exact(LevelBufs L, NodeArrays nd, const int64_t *box_base,
+                                                                 BoxStore B, MemberStore MS, const float *dnn,
+                                                                 rs_dev_status *st)
 {
-    const int b = blockIdx.x;
+    __shared__ int si_s[W_WARPS][W_STACK];
+    const int w = warp_id(), lane = lane_id();
+    const int b = blockIdx.x * W_WARPS + w;
+    if (b >= *L.band_len) return;
     const int k = L.band_rank[b], s = L.band_slot[b];
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
     const Metric6 met = L.met[k];
-    const float4 pq = wpos[s], vq = wvel[s];
+    const MemberStore M = mem_shift(MS, first);
+    const int q = s - first;
+    float4 pq, vq;
+    mem_get(M, q, pq, vq);
     const float lim = dnn[s] * (float)(1.0 + 2.0 * RS_BAND);
+    BvhView V;
+    bvh_view(V, B, box_base[k], n);
+    const int own = q / BVH_LEAF;
     double best = INFINITY;
-    for (int c = threadIdx.x; c < n; c += TQ) {
-        if (first + c == s) continue;
-        const float4 pc = wpos[first + c], vc = wvel[first + c];
-        if (d2_32(pq, vq, pc, vc, met) <= lim) best = fmin(best, d2_64(pq, vq, pc, vc, met));
+    {
+        const int m = own * BVH_LEAF + lane;
+        if (m < n && m != q) {
+            float4 pc, vc;
+            mem_get(M, m, pc, vc);
+            if (d2_32(pq, vq, pc, vc, met) <= lim) best = fmin(best, d2_64(pq, vq, pc, vc, met));
+        }
     }
-    best = warp_min(best);
-    __shared__ double w[TQ / 32];
-    if (lane_id() == 0) w[warp_id()] = best;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double m = w[0];
-        for (int i = 1; i < TQ / 32; i++) m = fmin(m, w[i]);
-        L.band_val[b] = m;
+    int *si = si_s[w];
+    if (V.H >= 2) {
+        if (lane == 0) si[0] = (V.H - 1) << 24;
+        int sp = 1;
+        __syncwarp();
+        for (int it = 0; sp > 0 && it < (1 << 24); it++) {
+            sp--;
+            const int ent = si[sp];
+            __syncwarp();
+            const int ch = (ent >> 24) - 1, c = 32 * (ent & 0xffffff) + lane;
+            const bool ok = c < V.cnt[ch] && !(ch == 0 && c == own) &&
+                            point_box_d2(pq, vq, box_get(V.S, V.off[ch] + c), met) <= lim * RS_PRUNE_SLACK;
+            unsigned mask = __ballot_sync(FULLW, ok);
+            if (ch == 0) {
+                while (mask) {
+                    const int src = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const int m = (32 * (ent & 0xffffff) + src) * BVH_LEAF + lane;
+                    if (m < n && m != q) {
+                        float4 pc, vc;
+                        mem_get(M, m, pc, vc);
+                        if (d2_32(pq, vq, pc, vc, met) <= lim) best = fmin(best, d2_64(pq, vq, pc, vc, met));
+                    }
+                }
+                continue;
+            }
+            if (sp + __popc(mask) > W_STACK) {
+                if (lane == 0) dev_fail(st, DEV_OVERFLOW, 57, node);
+                break;
+            }
+            if (ok) si[sp + __popc(mask & ((1u << lane) - 1u))] = (ch << 24) | c;
+            sp += __popc(mask);
+            __syncwarp();
+        }
     }
+    for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(FULLW, best, o));
+    if (lane == 0) L.band_val[b] = best;
 }
 
 __global__ void k_lvl_l2(LevelBufs L, NodeArrays nd, double f, rs_dev_status *st)
@@ -1996,10 +2043,17 @@ __global__ void k_lvl_comp(LevelBufs L, NodeArrays nd, const int *widx, int *par
     const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x];
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
     const int q = q0 + threadIdx.x;
-    if (q >= n) return;
-    int r = uf_find(parent, first + q, st);
-    atomicAdd(&csize[r], 1);
-    atomicMin(&cmin[r], widx[first + q]);
+    const bool ok = q < n;
+    const int r = ok ? uf_find(parent, first + q, st) : -1;
+    const int mi = ok ? widx[first + q] : 0x7fffffff;
+    // lanes of one component add once (consecutive members mostly share a root)
+    const unsigned grp = __match_any_sync(0xffffffffu, r);
+    const int lead = __ffs(grp) - 1;
+    const int gm = (int)__reduce_min_sync(grp, (unsigned)mi);
+    if (ok && lane_id() == lead) {
+        atomicAdd(&csize[r], __popc(grp));
+        atomicMin(&cmin[r], gm);
+    }
 }
 
 __global__ void k_lvl_keys(LevelBufs L, NodeArrays nd, int *parent, const int *csize, const int *cmin,
@@ -2416,8 +2470,8 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         int64_t NB;
         RS_TRY(rs_read_i64(ctx, ctr + 4, 1, &NB, "rs_refine6d"));
         const int nbv = (int)(NB & 0xffffffffll);
-        RS_LAUNCH(ctx, "rf_lvl_band_exact", k_lvl_band_exact, nbv, TQ, 0, L, nd, (const float4 *)wpos,
-                  (const float4 *)wvel, (const float *)dnn);
+        RS_LAUNCH(ctx, "rf_lvl_band_exact", k_lvl_band_exact, ceil_div(nbv, W_WARPS), W_WARPS * 32, 0, L, nd,
+                  (const int64_t *)bo, boxes, ms, (const float *)dnn, ctx->d_status);
         RS_LAUNCH(ctx, "rf_lvl_l2", k_lvl_l2, K, 128, 0, L, nd, f, ctx->d_status);
         RS_LAUNCH(ctx, "rf_lvl_iota", k_lvl_iota, T, TQ, 0, L, nd, uf, csize, cmin);
         RS_LAUNCH(ctx, "rf_bvh_linkbox", k_bvh_linkbox, K, 256, 0, L, nd, (const int64_t *)bo, boxes,
