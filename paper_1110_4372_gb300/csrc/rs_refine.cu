@@ -968,27 +968,51 @@ __device__ __forceinline__ void box_merge(Box6 &b, const Box6 &c)
     b.vhi.x = fmaxf(b.vhi.x, c.vhi.x); b.vhi.y = fmaxf(b.vhi.y, c.vhi.y); b.vhi.z = fmaxf(b.vhi.z, c.vhi.z);
 }
 
-// one block builds one node's hierarchy, level by level
-__global__ void __launch_bounds__(256) k_bvh_build(LevelBufs L, NodeArrays nd, const int64_t *box_base,
-                                                   BoxStore B, MemberStore MS, const float4 *wpos, const float4 *wvel)
+// float <-> int with the same order (finite values), for warp min/max votes
+__device__ __forceinline__ int ford_i(float f)
 {
-    const int k = blockIdx.x;
-    if (k >= L.K) return;
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+
+__device__ __forceinline__ float iord_f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__device__ __forceinline__ float wmin_f(float x) { return iord_f(__reduce_min_sync(0xffffffffu, ford_i(x))); }
+__device__ __forceinline__ float wmax_f(float x) { return iord_f(__reduce_max_sync(0xffffffffu, ford_i(x))); }
+
+// Leaf boxes and the packed member copy, one warp per leaf over the whole
+// level (tiles of 256 members, eight leaves each).
+__global__ void __launch_bounds__(TQ) k_bvh_leaves(LevelBufs L, NodeArrays nd, const int64_t *box_base, BoxStore B,
+                                                   MemberStore MS, const float4 *wpos, const float4 *wvel)
+{
+    const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x] + 32 * warp_id();
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
-    const int nl = (int)ceil_div(n, BVH_LEAF);
-    const BoxStore bx = box_shift(B, box_base[k]);
-    for (int m = threadIdx.x; m < n; m += blockDim.x) {
-        const float4 p = wpos[first + m], v = wvel[first + m];
+    if (q0 >= n) return;
+    const int m = q0 + lane_id();
+    const bool ok = m < n;
+    float4 p = make_float4(0, 0, 0, 0), v = p;
+    if (ok) {
+        p = wpos[first + m];
+        v = wvel[first + m];
         MS.a[first + m] = make_float4(p.x, p.y, p.z, v.x);
         MS.b[first + m] = make_float2(v.y, v.z);
     }
-    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
-        Box6 b = box_empty();
-        const int e = min(n, (i + 1) * BVH_LEAF);
-        for (int m = i * BVH_LEAF; m < e; m++) box_add(b, wpos[first + m], wvel[first + m]);
-        box_put(bx, i, b);
-    }
-    __syncthreads();
+    Box6 b;
+    b.plo = make_float4(wmin_f(ok ? p.x : INFINITY), wmin_f(ok ? p.y : INFINITY), wmin_f(ok ? p.z : INFINITY), 0.f);
+    b.phi = make_float4(wmax_f(ok ? p.x : -INFINITY), wmax_f(ok ? p.y : -INFINITY), wmax_f(ok ? p.z : -INFINITY), 0.f);
+    b.vlo = make_float4(wmin_f(ok ? v.x : INFINITY), wmin_f(ok ? v.y : INFINITY), wmin_f(ok ? v.z : INFINITY), 0.f);
+    b.vhi = make_float4(wmax_f(ok ? v.x : -INFINITY), wmax_f(ok ? v.y : -INFINITY), wmax_f(ok ? v.z : -INFINITY), 0.f);
+    if (lane_id() == 0) box_put(box_shift(B, box_base[k]), q0 / BVH_LEAF, b);
+}
+
+// one block per node: the levels above the leaves
+__global__ void __launch_bounds__(256) k_bvh_build(LevelBufs L, NodeArrays nd, const int64_t *box_base, BoxStore B)
+{
+    const int k = blockIdx.x;
+    if (k >= L.K) return;
+    const int node = L.list[k], n = nd.count[node];
+    const int nl = (int)ceil_div(n, BVH_LEAF);
+    const BoxStore bx = box_shift(B, box_base[k]);
     const int H = bvh_levels(nl);
     int64_t off_prev = 0, off = nl;
     int cprev = nl;
@@ -2401,8 +2425,9 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
             ms.a = carve<float4>(sp2, M);
             ms.b = carve<float2>(sp2, M);
         }
-        RS_LAUNCH(ctx, "rf_bvh_build", k_bvh_build, K, 256, 0, L, nd, (const int64_t *)bo, boxes, ms,
+        RS_LAUNCH(ctx, "rf_bvh_leaves", k_bvh_leaves, T, TQ, 0, L, nd, (const int64_t *)bo, boxes, ms,
                   (const float4 *)wpos, (const float4 *)wvel);
+        RS_LAUNCH(ctx, "rf_bvh_build", k_bvh_build, K, 256, 0, L, nd, (const int64_t *)bo, boxes);
         // ---- linking length: sampled bracket, bounded nearest neighbours, exact select ----
         RS_WS(ctx, int64_t, ch, WS_RF_MISC4, 2 * (K + 1) + 8);
         int64_t *nsm = ch, *stot = ch + (K + 1);
