@@ -56,90 +56,116 @@ __device__ __forceinline__ void load3(const float *a, int stride, int64_t i, flo
 // Per group and axis: shift coordinates in the upper half of the box down by
 // box if that makes the group's extent smaller than box/2 (bit a of
 // shift[g]); minidx of the group.  One block per group.
-__global__ void k_group_unwrap(int64_t G, const int64_t *off, const int32_t *perm, int64_t n, const float *pos,
-                               int stride, float boxf, int *shift_bits, int *gmin, rs_dev_status *st)
+// float <-> int with the same order (finite values and infinities)
+__device__ __forceinline__ int ord_i(float f)
 {
-    __shared__ float red12[32][12];
-    __shared__ int redi[32];
-    for (int64_t g = blockIdx.x; g < G; g += gridDim.x) {
-        const int64_t a = off[g], b = off[g + 1];
-        // minima of x and -x, unshifted and shifted, per axis
-        float r[12];
-        for (int k = 0; k < 12; k++) r[k] = INFINITY;
-        int mn = 0x7fffffff;
-        if (b < a) dev_fail(st, DEV_BADARG, 32, g);
-        for (int64_t m = a + threadIdx.x; m < b; m += blockDim.x) {
-            int i = perm[m];
-            if (i < 0 || i >= n) {
-                dev_fail(st, DEV_BADARG, 33, m);
-                continue;
-            }
-            mn = min(mn, i);
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+
+__device__ __forceinline__ float ord_f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__global__ void k_fill_s32(int32_t *p, int64_t n, int32_t v)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+// group of member slot m (off[g] <= base + m < off[g + 1])
+__device__ __forceinline__ int64_t group_of(const int64_t *off, int64_t G, int64_t at)
+{
+    int64_t lo = 0, hi = G;  // off[lo] <= at < off[hi]
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= at) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Unwrap decision inputs, one member per thread over all groups: per group
+// and axis the minima of x and -x, unshifted and with the upper half of the
+// box shifted down by the box, and the smallest particle index.  Lanes of
+// one group (groups are contiguous runs of slots) combine before their
+// atomics, kept on order-preserving integer images of the floats.
+__global__ void k_unwrap_tiles(int64_t G, const int64_t *off, const int32_t *perm, int64_t n, int64_t M,
+                               const float *pos, int stride, float boxf, int *slot_group, int *gred, int *gmin,
+                               rs_dev_status *st)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = m < M;
+    int g = -1, i = 0x7fffffff;
+    float r[12];
+    for (int k = 0; k < 12; k++) r[k] = INFINITY;
+    if (ok) {
+        g = (int)group_of(off, G, off[0] + m);
+        slot_group[m] = g;
+        i = perm[off[0] + m];
+        if (i < 0 || i >= n) {
+            dev_fail(st, DEV_BADARG, 33, m);
+            i = 0x7fffffff;
+        } else {
             float c[3];
             load3(pos, stride, i, c[0], c[1], c[2]);
             for (int d = 0; d < 3; d++) {
-                float s = c[d] >= 0.5f * boxf ? c[d] - boxf : c[d];
-                r[d] = fminf(r[d], c[d]);
-                r[3 + d] = fminf(r[3 + d], -c[d]);
-                r[6 + d] = fminf(r[6 + d], s);
-                r[9 + d] = fminf(r[9 + d], -s);
+                const float sft = c[d] >= 0.5f * boxf ? c[d] - boxf : c[d];
+                r[d] = c[d];
+                r[3 + d] = -c[d];
+                r[6 + d] = sft;
+                r[9 + d] = -sft;
             }
         }
-        for (int k = 0; k < 12; k++) r[k] = warp_min(r[k]);
-        mn = warp_min(mn);
-        if (lane_id() == 0) {
-            for (int k = 0; k < 12; k++) red12[warp_id()][k] = r[k];
-            redi[warp_id()] = mn;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int m2 = 0x7fffffff;
-            for (int k = 0; k < 12; k++) r[k] = INFINITY;
-            for (int w = 0; w < (int)(blockDim.x / 32); w++) {
-                for (int k = 0; k < 12; k++) r[k] = fminf(r[k], red12[w][k]);
-                m2 = min(m2, redi[w]);
-            }
-            int bits = 0;
-            for (int d = 0; d < 3; d++) {
-                float ext = -r[3 + d] - r[d];
-                float exts = -r[9 + d] - r[6 + d];
-                if (ext < 0.5f * boxf) {
-                } else if (exts < 0.5f * boxf) {
-                    bits |= 1 << d;
-                } else {
-                    dev_fail(st, DEV_EXTENT, 30, g);
-                }
-            }
-            shift_bits[g] = bits;
-            gmin[g] = m2;
-        }
-        __syncthreads();
+    }
+    const unsigned grp = __match_any_sync(0xffffffffu, g);
+    const int lead = __ffs(grp) - 1;
+    int v[12];
+    for (int k = 0; k < 12; k++) v[k] = __reduce_min_sync(grp, ord_i(r[k]));
+    const int mi = (int)__reduce_min_sync(grp, (unsigned)i);
+    if (ok && lane_id() == lead) {
+        for (int k = 0; k < 12; k++) atomicMin(&gred[12 * (int64_t)g + k], v[k]);
+        atomicMin(&gmin[g], mi);
     }
 }
 
-__global__ void k_gather(int64_t G, const int64_t *off, const int32_t *perm, int64_t n, const float *pos,
-                         const float *vel, int stride, float boxf, const int *shift_bits, float4 *wpos, float4 *wvel, int *widx,
-                         int *slot_group)
+// per group: which axes wrap (the group spans less than half the box once
+// the upper half is shifted down), or an extent error
+__global__ void k_unwrap_bits(int64_t G, const int *gred, float boxf, int *shift_bits, rs_dev_status *st)
 {
-    // one block per group, grid-stride
-    for (int64_t g = blockIdx.x; g < G; g += gridDim.x) {
-        const int64_t a = off[g], b = off[g + 1], base = off[0];
-        const int bits = shift_bits[g];
-        for (int64_t m = a + threadIdx.x; m < b; m += blockDim.x) {
-            int i = perm[m];
-            if (i < 0 || i >= n) i = 0;  // recorded by k_group_unwrap
-            float x, y, z, u, v, w;
-            load3(pos, stride, i, x, y, z);
-            load3(vel, stride, i, u, v, w);
-            if ((bits & 1) && x >= 0.5f * boxf) x = x - boxf;
-            if ((bits & 2) && y >= 0.5f * boxf) y = y - boxf;
-            if ((bits & 4) && z >= 0.5f * boxf) z = z - boxf;
-            wpos[m - base] = make_float4(x, y, z, 0.f);
-            wvel[m - base] = make_float4(u, v, w, 0.f);
-            widx[m - base] = i;
-            slot_group[m - base] = (int)g;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const int *r = gred + 12 * g;
+    int bits = 0;
+    for (int d = 0; d < 3; d++) {
+        const float ext = -ord_f(r[3 + d]) - ord_f(r[d]);
+        const float exts = -ord_f(r[9 + d]) - ord_f(r[6 + d]);
+        if (ext < 0.5f * boxf) {
+        } else if (exts < 0.5f * boxf) {
+            bits |= 1 << d;
+        } else {
+            dev_fail(st, DEV_EXTENT, 30, g);
         }
     }
+    shift_bits[g] = bits;
+}
+
+__global__ void k_gather(int64_t M, const int64_t *off, const int32_t *perm, int64_t n, const float *pos,
+                         const float *vel, int stride, float boxf, const int *slot_group, const int *shift_bits,
+                         float4 *wpos, float4 *wvel, int *widx)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const int bits = shift_bits[slot_group[m]];
+    int i = perm[off[0] + m];
+    if (i < 0 || i >= n) i = 0;  // recorded by k_unwrap_tiles
+    float x, y, z, u, v, w;
+    load3(pos, stride, i, x, y, z);
+    load3(vel, stride, i, u, v, w);
+    if ((bits & 1) && x >= 0.5f * boxf) x = x - boxf;
+    if ((bits & 2) && y >= 0.5f * boxf) y = y - boxf;
+    if ((bits & 4) && z >= 0.5f * boxf) z = z - boxf;
+    wpos[m] = make_float4(x, y, z, 0.f);
+    wvel[m] = make_float4(u, v, w, 0.f);
+    widx[m] = i;
 }
 
 __global__ void k_check_offsets(int64_t G, const int64_t *off, rs_dev_status *st)
@@ -968,17 +994,9 @@ __device__ __forceinline__ void box_merge(Box6 &b, const Box6 &c)
     b.vhi.x = fmaxf(b.vhi.x, c.vhi.x); b.vhi.y = fmaxf(b.vhi.y, c.vhi.y); b.vhi.z = fmaxf(b.vhi.z, c.vhi.z);
 }
 
-// float <-> int with the same order (finite values), for warp min/max votes
-__device__ __forceinline__ int ford_i(float f)
-{
-    const int i = __float_as_int(f);
-    return i >= 0 ? i : i ^ 0x7fffffff;
-}
-
-__device__ __forceinline__ float iord_f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
-
-__device__ __forceinline__ float wmin_f(float x) { return iord_f(__reduce_min_sync(0xffffffffu, ford_i(x))); }
-__device__ __forceinline__ float wmax_f(float x) { return iord_f(__reduce_max_sync(0xffffffffu, ford_i(x))); }
+// warp min/max votes on order-preserving integer images
+__device__ __forceinline__ float wmin_f(float x) { return ord_f(__reduce_min_sync(0xffffffffu, ord_i(x))); }
+__device__ __forceinline__ float wmax_f(float x) { return ord_f(__reduce_max_sync(0xffffffffu, ord_i(x))); }
 
 // Leaf boxes and the packed member copy, one warp per leaf over the whole
 // level (tiles of 256 members, eight leaves each).
@@ -2274,8 +2292,8 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
     RS_WS(ctx, int, uf, WS_RF_PARENT, 3 * M);
     int *csize = uf + M, *cmin = uf + 2 * M;
     int *widx = t->members;
-    RS_WS(ctx, int, gmisc, WS_RF_MISC0, 2 * G + 2 * M + 8);
-    int *shift_bits = gmisc, *gmin = gmisc + G, *slot_group = gmisc + 2 * G;
+    RS_WS(ctx, int, gmisc, WS_RF_MISC0, 14 * G + 2 * M + 8);
+    int *shift_bits = gmisc, *gmin = gmisc + G, *slot_group = gmisc + 2 * G, *gred = gmisc + 2 * G + M;
     // node queues: big lists (ping-pong) and the small queue; counters
     // counters first (16 ints = 64 bytes, so everything after stays 8-byte aligned)
     RS_WS(ctx, int, q, WS_RF_NODEQ, 4 * cap + 16);
@@ -2285,10 +2303,15 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
     RS_CUDA(ctx, cudaMemsetAsync(ctr, 0, sizeof(int) * 16, ctx->stream));
 
     const int gb = (int)std::min<int64_t>(G, (int64_t)ctx->num_sms * 8);
-    RS_LAUNCH(ctx, "rf_group_unwrap", k_group_unwrap, gb, 256, 0, G, goff, perm, n, pos, stride, boxf, shift_bits, gmin,
+    RS_LAUNCH(ctx, "rf_unwrap_init", k_fill_s32, ceil_div(12 * G, 256), 256, 0, (int32_t *)gred, 12 * G,
+              (int32_t)0x7f800000);
+    RS_LAUNCH(ctx, "rf_unwrap_init", k_fill_s32, ceil_div(G, 256), 256, 0, (int32_t *)gmin, G, (int32_t)0x7fffffff);
+    RS_LAUNCH(ctx, "rf_group_unwrap", k_unwrap_tiles, ceil_div(M, 256), 256, 0, G, goff, perm, n, M, pos, stride,
+              boxf, slot_group, gred, gmin, ctx->d_status);
+    RS_LAUNCH(ctx, "rf_unwrap_bits", k_unwrap_bits, ceil_div(G, 256), 256, 0, G, (const int *)gred, boxf, shift_bits,
               ctx->d_status);
-    RS_LAUNCH(ctx, "rf_gather", k_gather, gb, 256, 0, G, goff, perm, n, pos, vel, stride, boxf,
-              (const int *)shift_bits, wpos, wvel, widx, slot_group);
+    RS_LAUNCH(ctx, "rf_gather", k_gather, ceil_div(M, 256), 256, 0, M, goff, perm, n, pos, vel, stride, boxf,
+              (const int *)slot_group, (const int *)shift_bits, wpos, wvel, widx);
     RS_LAUNCH(ctx, "rf_roots", k_make_roots, ceil_div(G, 256), 256, 0, G, goff, (const int *)gmin,
               (const int *)shift_bits, (int)min_n, nd,
               big_a, ctr + 0, small_q, ctr + 2, ctx->d_status);
