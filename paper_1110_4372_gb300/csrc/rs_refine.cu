@@ -2378,9 +2378,10 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         RS_WS(ctx, uint32_t, v1, WS_SORT_V1, LM);
         int rbits = 0;
         while (rbits < 32 && ((uint64_t)(K - 1) >> rbits) != 0) rbits++;
-        if (level == 0) {
-            // order each big root's members by k-d splits at leaf-aligned
-            // medians; children keep this order through the stable child
+        if (level <= 1) {
+            // order each big node's members by k-d splits at leaf-aligned
+            // medians (levels 0 and 1, where most of the search work is);
+            // deeper levels keep this order through the stable child
             // partition below
             int64_t maxn = 0;
             RS_TRY(rs_read_i64(ctx, tot + 3, 1, &maxn, "rs_refine6d"));
