@@ -56,8 +56,8 @@ BYTES_ASSIGN_PER_MEMBER = 28
 # scaled to a step by the units processed.  An entry is dropped when its
 # kernel changes.
 NCU_TRAFFIC_PER_UNIT = {
-    "rf_lvl_link": 326767104 / 8612074,
-    "rf_lvl_nn": 244146944 / 8612074,
+    "rf_lvl_link": 329032000 / 8612074,
+    "rf_lvl_nn": 243618000 / 8612074,
 }
 
 # Which units each kernel processes per step (for its algorithmic bytes).
@@ -297,13 +297,20 @@ def main():
         if dist:
             dist.barrier()
         k = max(1, min(args.steps, 3))
+        esampler = ClockSampler(local)
+        esampler.start()
+        calls = []
         t0 = time.perf_counter()
         for _ in range(k):
+            t1 = time.perf_counter()
             rsgpu.rs_find_halos(ctx, hp, hv, cat.box, p, halo_id=hout)
+            calls.append(1e3 * (time.perf_counter() - t1))
         torch.cuda.synchronize()
         dt = max_over_ranks((time.perf_counter() - t0) / k, dist)
+        eclocks = esampler.stop()
         e2e = {"value": whole_job_rate(n, world, dt), "unit": "particles/s", "h2d_bytes_per_step": 2 * 12 * n,
-               "d2h_bytes_per_step": 4 * n, "ms_per_step": 1e3 * dt}
+               "d2h_bytes_per_step": 4 * n, "ms_per_step": 1e3 * dt, "ms_per_call": [round(c, 1) for c in calls],
+               "clocks": eclocks}
 
     if rank != 0:
         if dist:
