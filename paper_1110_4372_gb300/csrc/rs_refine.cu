@@ -37,6 +37,8 @@ namespace {
 constexpr int SMALL_N = 1024;       // largest node handled by one CTA
 constexpr int SMALL_THREADS = 256;
 constexpr int STACK_CAP = 256;
+constexpr int MID_N = 128;          // largest node of the middle CTA size
+constexpr int MID_THREADS = 128;
 constexpr int TINY_N = 32;          // largest node handled by one warp
 constexpr int TINY_WARPS = 8;       // warps per block of the tiny-node kernel
 constexpr int TINY_STACK = 32;      // pending nodes per warp
@@ -207,20 +209,21 @@ __global__ void k_make_roots(int64_t G, const int64_t *off, const int *gmin, con
 // ---------------------------------------------------------------------------
 // small nodes: whole subtree in one CTA
 // ---------------------------------------------------------------------------
+template <int NMAX, int NT>
 struct SmallShared {
-    float px[SMALL_N], py[SMALL_N], pz[SMALL_N], vx[SMALL_N], vy[SMALL_N], vz[SMALL_N];
-    int idx[SMALL_N];
-    float dnn[SMALL_N];
-    int par[SMALL_N];
-    int csize[SMALL_N];
-    int cmin[SMALL_N];
-    unsigned long long key[SMALL_N];
-    float tp[6][SMALL_N];
-    int tidx[SMALL_N];
+    float px[NMAX], py[NMAX], pz[NMAX], vx[NMAX], vy[NMAX], vz[NMAX];
+    int idx[NMAX];
+    float dnn[NMAX];
+    int par[NMAX];
+    int csize[NMAX];
+    int cmin[NMAX];
+    unsigned long long key[NMAX];
+    float tp[6][NMAX];
+    int tidx[NMAX];
     int4 stack[STACK_CAP];
     int sp;
     int job;
-    MomAcc wacc[SMALL_THREADS / 32];
+    MomAcc wacc[NT / 32];
     Metric6 met;
     double l2;
     float lo32, hi32, tlo32, thi32;
@@ -228,11 +231,13 @@ struct SmallShared {
     int pick;
 };
 
-__device__ __forceinline__ float4 sp4(const SmallShared &S, int i)
+template <class SS>
+__device__ __forceinline__ float4 sp4(const SS &S, int i)
 {
     return make_float4(S.px[i], S.py[i], S.pz[i], 0.f);
 }
-__device__ __forceinline__ float4 sv4(const SmallShared &S, int i)
+template <class SS>
+__device__ __forceinline__ float4 sv4(const SS &S, int i)
 {
     return make_float4(S.vx[i], S.vy[i], S.vz[i], 0.f);
 }
@@ -257,12 +262,17 @@ __device__ void bitonic_u64(unsigned long long *key, int P)
     }
 }
 
-__global__ void __launch_bounds__(SMALL_THREADS, 2)
+// One CTA of NT threads per subtree of at most NMAX members; nodes of at most
+// `fwd_limit` members (roots or children) go to the next queue, whose kernel
+// runs after this one (members are written back in their final order).
+template <int NMAX, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
     k_small_subtree(const int *queue, const int *queue_len, int *queue_head, float4 *wpos, float4 *wvel, int *widx,
-                    int *tiny_q, int *tiny_len, NodeArrays nd, double box, double f, int min_n, rs_dev_status *st)
+                    int fwd_limit, int *fwd_q, int *fwd_len, NodeArrays nd, double box, double f, int min_n,
+                    rs_dev_status *st)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmallShared &S = *reinterpret_cast<SmallShared *>(smem_raw);
+    SmallShared<NMAX, NT> &S = *reinterpret_cast<SmallShared<NMAX, NT> *>(smem_raw);
     const int tid = threadIdx.x;
     for (;;) {
         if (tid == 0) S.job = atomicAdd(queue_head, 1);
@@ -273,11 +283,11 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
         const int node0 = queue[job];
         const int base = nd.first[node0];
         const int n0 = nd.count[node0];
-        if (n0 <= TINY_N) {  // a tiny subtree: one warp of the tiny-node kernel
-            if (tid == 0) tiny_q[atomicAdd(tiny_len, 1)] = node0;
+        if (n0 <= fwd_limit) {  // a subtree for the next, smaller kernel
+            if (tid == 0) fwd_q[atomicAdd(fwd_len, 1)] = node0;
             continue;
         }
-        for (int i = tid; i < n0; i += SMALL_THREADS) {
+        for (int i = tid; i < n0; i += NT) {
             float4 p = wpos[base + i], v = wvel[base + i];
             S.px[i] = p.x;
             S.py[i] = p.y;
@@ -305,13 +315,13 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
                 MomRef ref = mom_ref(sp4(S, lf), sv4(S, lf));
                 MomAcc a;
                 mom_zero(a);
-                for (int i = lf + tid; i < lf + cnt; i += SMALL_THREADS) mom_add(a, sp4(S, i), sv4(S, i), ref);
+                for (int i = lf + tid; i < lf + cnt; i += NT) mom_add(a, sp4(S, i), sv4(S, i), ref);
                 mom_warp_reduce(a);
                 if (lane_id() == 0) S.wacc[warp_id()] = a;
                 __syncthreads();
                 if (tid == 0) {
                     MomAcc t = S.wacc[0];
-                    for (int w = 1; w < SMALL_THREADS / 32; w++) mom_merge(t, S.wacc[w]);
+                    for (int w = 1; w < NT / 32; w++) mom_merge(t, S.wacc[w]);
                     MomOut o = mom_finalize(t, sp4(S, lf), sv4(S, lf), cnt, box);
                     for (int d = 0; d < 3; d++) {
                         nd.xbar[3 * node + d] = o.xbar[d];
@@ -329,7 +339,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
             }
             const Metric6 met = S.met;
             // ---- nearest neighbours (float32) ----
-            for (int q = lf + tid; q < lf + cnt; q += SMALL_THREADS) {
+            for (int q = lf + tid; q < lf + cnt; q += NT) {
                 const float4 pq = sp4(S, q), vq = sv4(S, q);
                 float best = INFINITY;
                 for (int c = lf; c < lf + cnt; c++) {
@@ -343,7 +353,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
             // ---- k-th smallest, float32 ----
             int P = 1;
             while (P < cnt) P <<= 1;
-            for (int i = tid; i < P; i += SMALL_THREADS)
+            for (int i = tid; i < P; i += NT)
                 S.key[i] = i < cnt ? (unsigned long long)__float_as_uint(S.dnn[lf + i]) : ~0ull;
             __syncthreads();
             bitonic_u64(S.key, P);
@@ -358,7 +368,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
             // (one warp per band member, lanes over the candidates)
             double *bval = reinterpret_cast<double *>(S.key);
             int *blist = S.tidx;
-            for (int q = lf + tid; q < lf + cnt; q += SMALL_THREADS) {
+            for (int q = lf + tid; q < lf + cnt; q += NT) {
                 const float dq = S.dnn[q];
                 if (dq < blo)
                     atomicAdd(&S.below, 1);
@@ -366,7 +376,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
                     blist[atomicAdd(&S.nband, 1)] = q;
             }
             __syncthreads();
-            for (int b = warp_id(); b < S.nband; b += SMALL_THREADS / 32) {
+            for (int b = warp_id(); b < S.nband; b += NT / 32) {
                 const int q = blist[b];
                 const float4 pq = sp4(S, q), vq = sv4(S, q);
                 const float lim = S.dnn[q] * (float)(1.0 + 2.0 * RS_BAND);
@@ -386,7 +396,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
                 if (want < 0 || want >= nb) {
                     if (tid == 0) dev_fail(st, DEV_INTERNAL, 40, node);
                 }
-                for (int b = tid; b < nb; b += SMALL_THREADS) {
+                for (int b = tid; b < nb; b += NT) {
                     int r = 0;
                     const double vb = bval[b];
                     for (int c = 0; c < nb; c++) r += (bval[c] < vb || (bval[c] == vb && c < b)) ? 1 : 0;
@@ -402,7 +412,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
                 S.thi32 = (float)(l2 * (1.0 + 3e-6));
                 nd.lnk[node] = sqrt(l2 / met.scale);
             }
-            for (int i = lf + tid; i < lf + cnt; i += SMALL_THREADS) S.par[i] = i;
+            for (int i = lf + tid; i < lf + cnt; i += NT) S.par[i] = i;
             __syncthreads();
             // ---- friends-of-friends at l (inclusive) ----
             {
@@ -412,7 +422,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
                 int tie = 0;
                 // warp-uniform candidate loop from the warp's first query: the
                 // candidate test and its loads are the same for every lane
-                for (int qb = lf + 32 * warp_id(); qb < lf + cnt; qb += SMALL_THREADS) {
+                for (int qb = lf + 32 * warp_id(); qb < lf + cnt; qb += NT) {
                     const int q = qb + lane_id();
                     const bool act = q < lf + cnt && S.dnn[q] <= part;
                     if (!__any_sync(0xffffffffu, act)) continue;
@@ -438,12 +448,12 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
             }
             __syncthreads();
             // ---- components ----
-            for (int i = lf + tid; i < lf + cnt; i += SMALL_THREADS) {
+            for (int i = lf + tid; i < lf + cnt; i += NT) {
                 S.csize[i] = 0;
                 S.cmin[i] = 0x7fffffff;
             }
             __syncthreads();
-            for (int i = lf + tid; i < lf + cnt; i += SMALL_THREADS) {
+            for (int i = lf + tid; i < lf + cnt; i += NT) {
                 int r = uf_find_s(S.par, i);
                 S.par[i] = r;
                 atomicAdd(&S.csize[r], 1);
@@ -451,7 +461,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
             }
             __syncthreads();
             // ---- children first (by smallest particle index), then the rest ----
-            for (int i = tid; i < P; i += SMALL_THREADS) {
+            for (int i = tid; i < P; i += NT) {
                 unsigned long long k = ~0ull;
                 if (i < cnt) {
                     int r = S.par[lf + i];
@@ -463,7 +473,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
             }
             __syncthreads();
             bitonic_u64(S.key, P);
-            for (int p = tid; p < cnt; p += SMALL_THREADS) {
+            for (int p = tid; p < cnt; p += NT) {
                 int o = lf + (int)(S.key[p] & 0xffffffffu);
                 S.tp[0][p] = S.px[o];
                 S.tp[1][p] = S.py[o];
@@ -474,7 +484,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
                 S.tidx[p] = S.idx[o];
             }
             __syncthreads();
-            for (int p = tid; p < cnt; p += SMALL_THREADS) {
+            for (int p = tid; p < cnt; p += NT) {
                 S.px[lf + p] = S.tp[0][p];
                 S.py[lf + p] = S.tp[1][p];
                 S.pz[lf + p] = S.tp[2][p];
@@ -484,7 +494,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
                 S.idx[lf + p] = S.tidx[p];
             }
             __syncthreads();
-            for (int p = tid; p < cnt; p += SMALL_THREADS) {
+            for (int p = tid; p < cnt; p += NT) {
                 const unsigned hiw = (unsigned)(S.key[p] >> 32);
                 if (hiw == 0xffffffffu) continue;
                 if (p > 0 && (unsigned)(S.key[p - 1] >> 32) == hiw) continue;
@@ -505,8 +515,8 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
                 nd.root[id] = nd.root[node];
                 nd.shift[id] = nd.shift[node];
                 atomicAdd(&S.nchild, 1);
-                if (e - p <= TINY_N) {  // its subtree goes to the tiny-node kernel
-                    tiny_q[atomicAdd(tiny_len, 1)] = id;
+                if (e - p <= fwd_limit) {  // its subtree goes to the next, smaller kernel
+                    fwd_q[atomicAdd(fwd_len, 1)] = id;
                     continue;
                 }
                 int s = atomicAdd(&S.sp, 1);
@@ -525,7 +535,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2)
             __syncthreads();
         }
         // members in their final order (the tiny-node kernel reads its nodes here)
-        for (int i = tid; i < n0; i += SMALL_THREADS) {
+        for (int i = tid; i < n0; i += NT) {
             widx[base + i] = S.idx[i];
             wpos[base + i] = make_float4(S.px[i], S.py[i], S.pz[i], 0.f);
             wvel[base + i] = make_float4(S.vx[i], S.vy[i], S.vz[i], 0.f);
@@ -2296,10 +2306,12 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
     int *shift_bits = gmisc, *gmin = gmisc + G, *slot_group = gmisc + 2 * G, *gred = gmisc + 2 * G + M;
     // node queues: big lists (ping-pong) and the small queue; counters
     // counters first (16 ints = 64 bytes, so everything after stays 8-byte aligned)
-    RS_WS(ctx, int, q, WS_RF_NODEQ, 4 * cap + 16);
-    int *ctr = q, *big_a = q + 16, *big_b = q + 16 + cap, *small_q = q + 16 + 2 * cap, *tiny_q = q + 16 + 3 * cap;
+    RS_WS(ctx, int, q, WS_RF_NODEQ, 5 * cap + 16);
+    int *ctr = q, *big_a = q + 16, *big_b = q + 16 + cap, *small_q = q + 16 + 2 * cap, *tiny_q = q + 16 + 3 * cap,
+        *mid_q = q + 16 + 4 * cap;
     // ctr: [0] big_a len, [1] big_b len, [2] small len, [3] small head, [4] band len,
-    // [6..7] bracket fallback flag, [8] tiny len, [9] tiny head
+    // [6..7] bracket fallback flag, [8] tiny len, [9] tiny head, [10] k-d ranges,
+    // [11] middle len, [12] middle head
     RS_CUDA(ctx, cudaMemsetAsync(ctr, 0, sizeof(int) * 16, ctx->stream));
 
     const int gb = (int)std::min<int64_t>(G, (int64_t)ctx->num_sms * 8);
@@ -2555,11 +2567,21 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
     }
 
     // ---- small nodes: whole subtrees ----
-    const size_t smem = sizeof(SmallShared);
-    RS_CUDA(ctx, cudaFuncSetAttribute(k_small_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    RS_LAUNCH(ctx, "rf_small_subtree", k_small_subtree, (int64_t)ctx->num_sms * 2, SMALL_THREADS, smem,
-              (const int *)small_q, (const int *)(ctr + 2), ctr + 3, wpos, wvel, widx, tiny_q, ctr + 8, nd, box, f,
-              (int)min_n, ctx->d_status);
+    // three size classes, each forwarding its smaller subtrees to the next
+    {
+        auto kbig = k_small_subtree<SMALL_N, SMALL_THREADS, 2>;
+        auto kmid = k_small_subtree<MID_N, MID_THREADS, 4>;
+        const size_t sbig = sizeof(SmallShared<SMALL_N, SMALL_THREADS>);
+        const size_t smid = sizeof(SmallShared<MID_N, MID_THREADS>);
+        RS_CUDA(ctx, cudaFuncSetAttribute(kbig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbig));
+        RS_CUDA(ctx, cudaFuncSetAttribute(kmid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smid));
+        RS_LAUNCH(ctx, "rf_small_subtree", kbig, (int64_t)ctx->num_sms * 2, SMALL_THREADS, sbig, (const int *)small_q,
+                  (const int *)(ctr + 2), ctr + 3, wpos, wvel, widx, MID_N, mid_q, ctr + 11, nd, box, f, (int)min_n,
+                  ctx->d_status);
+        RS_LAUNCH(ctx, "rf_mid_subtree", kmid, (int64_t)ctx->num_sms * 4, MID_THREADS, smid, (const int *)mid_q,
+                  (const int *)(ctr + 11), ctr + 12, wpos, wvel, widx, TINY_N, tiny_q, ctr + 8, nd, box, f,
+                  (int)min_n, ctx->d_status);
+    }
     RS_LAUNCH(ctx, "rf_tiny_subtree", k_tiny_subtree, (int64_t)ctx->num_sms * 8, TINY_WARPS * 32, 0,
               (const int *)tiny_q, (const int *)(ctr + 8), ctr + 9, (const float4 *)wpos, (const float4 *)wvel, widx,
               nd, box, f, (int)min_n, ctx->d_status);
