@@ -37,7 +37,7 @@ namespace {
 constexpr int SMALL_N = 1024;       // largest node handled by one CTA
 constexpr int SMALL_THREADS = 256;
 constexpr int STACK_CAP = 256;
-constexpr int MID_N = 128;          // largest node of the middle CTA size
+constexpr int MID_N = 256;          // largest node of the middle CTA size
 constexpr int MID_THREADS = 128;
 constexpr int TINY_N = 32;          // largest node handled by one warp
 constexpr int TINY_WARPS = 8;       // warps per block of the tiny-node kernel
