@@ -1449,7 +1449,7 @@ __device__ __forceinline__ bool link_child(const BvhView &V, int ent, int lane, 
 
 constexpr int LK_STACK = 256;  // link stack entries per warp
 constexpr int LK_LEAVES = 128; // pending leaves per warp
-constexpr int LK_BATCH = 4;    // leaves scanned together
+constexpr int LK_BATCH = 2;    // leaves scanned together
 
 // Friends-of-friends pairs of member q with the members after it (outside
 // its own leaf) by a whole warp; returns this lane's tie count.  The search
