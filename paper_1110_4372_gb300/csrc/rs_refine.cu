@@ -1535,7 +1535,7 @@ __device__ __forceinline__ int w32_link(const BvhView &V, const MemberStore &M, 
 // friends-of-friends at l, one warp per leaf of 32 consecutive members, pairs
 // with the candidate after the query in the node's member order; only
 // members with a neighbour within reach take part
-__global__ void __launch_bounds__(TQ) k_bvh_link(LevelBufs L, NodeArrays nd, const int64_t *box_base,
+__global__ void __launch_bounds__(TQ, 4) k_bvh_link(LevelBufs L, NodeArrays nd, const int64_t *box_base,
                                                  BoxStore B, MemberStore MS, const float *dnn, int *parent,
                                                  rs_dev_status *st)
 {
