@@ -1310,7 +1310,7 @@ __device__ __forceinline__ float w32_nn(const BvhView &V, const MemberStore &M, 
 // nearest-neighbour distances, one warp per job of 32 consecutive members
 // (one leaf): the leaf is held in registers, one member per lane, and its 32
 // queries are searched one after another
-__global__ void __launch_bounds__(W_WARPS * 32) k_bvh_nn(LevelBufs L, WarpJobs J, NodeArrays nd,
+__global__ void __launch_bounds__(W_WARPS * 32, 6) k_bvh_nn(LevelBufs L, WarpJobs J, NodeArrays nd,
                                                          const int64_t *box_base, BoxStore B, MemberStore MS,
                                                          const float *R2, const float *STOP, float *out,
                                                          rs_dev_status *st)
