@@ -217,7 +217,7 @@ __device__ __forceinline__ int nth_bit64(uint64_t m, int j)
 // cells; the warp then numbers all lanes' candidates (a prefix sum of the
 // mask popcounts) and deals them out 32 at a time, so each lane tests one
 // candidate pair per round whatever the spread of candidates over the cells.
-__global__ void __launch_bounds__(FOF_THREADS) k_fof_link(const uint32_t *n_cells_p, const uint64_t *cell_key,
+__global__ void __launch_bounds__(FOF_THREADS, 6) k_fof_link(const uint32_t *n_cells_p, const uint64_t *cell_key,
                                                             const uint32_t *cell_start, const uint32_t *table,
                                                             const uint64_t *occ, const float4 *spos, int *parent,
                                                             FofGeom g, int pass, rs_dev_status *st)

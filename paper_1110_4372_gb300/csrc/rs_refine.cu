@@ -2570,7 +2570,7 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
     // three size classes, each forwarding its smaller subtrees to the next
     {
         auto kbig = k_small_subtree<SMALL_N, SMALL_THREADS, 2>;
-        auto kmid = k_small_subtree<MID_N, MID_THREADS, 4>;
+        auto kmid = k_small_subtree<MID_N, MID_THREADS, 8>;
         const size_t sbig = sizeof(SmallShared<SMALL_N, SMALL_THREADS>);
         const size_t smid = sizeof(SmallShared<MID_N, MID_THREADS>);
         RS_CUDA(ctx, cudaFuncSetAttribute(kbig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbig));
@@ -2578,7 +2578,7 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         RS_LAUNCH(ctx, "rf_small_subtree", kbig, (int64_t)ctx->num_sms * 2, SMALL_THREADS, sbig, (const int *)small_q,
                   (const int *)(ctr + 2), ctr + 3, wpos, wvel, widx, MID_N, mid_q, ctr + 11, nd, box, f, (int)min_n,
                   ctx->d_status);
-        RS_LAUNCH(ctx, "rf_mid_subtree", kmid, (int64_t)ctx->num_sms * 4, MID_THREADS, smid, (const int *)mid_q,
+        RS_LAUNCH(ctx, "rf_mid_subtree", kmid, (int64_t)ctx->num_sms * 8, MID_THREADS, smid, (const int *)mid_q,
                   (const int *)(ctr + 11), ctr + 12, wpos, wvel, widx, TINY_N, tiny_q, ctr + 8, nd, box, f,
                   (int)min_n, ctx->d_status);
     }
