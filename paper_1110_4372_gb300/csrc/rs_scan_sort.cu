@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const K *keys, int64
 // shared memory in digit order, then written out in that order, so the
 // items of one digit go to consecutive global slots (coalesced stores).
 template <typename K>
-__global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const K *kin, K *kout, const uint32_t *vin,
+__global__ void __launch_bounds__(SORT_THREADS, 4) k_sort_scatter(const K *kin, K *kout, const uint32_t *vin,
                                                                  uint32_t *vout, int64_t n, int shift,
                                                                  const uint32_t *hist, int64_t ntiles)
 {
