@@ -6,19 +6,24 @@
 // group straddles a face).  Nodes own nested slot ranges: a node's children
 // occupy the front of its range.
 //
-// Three size classes:
-//  * tiny nodes (<= TINY_N = 32 members): one warp holds the node in
-//    registers, a member per lane, and builds its whole subtree with warp
-//    shuffles and votes, eight subtrees per CTA at a time;
+// Size classes:
+//  * big nodes (> SMALL_N members): processed level by level by tiles of 256
+//    members spread over the whole GPU, with per-node accumulators and
+//    histograms in global memory.  At levels 0 and 1 their members are put in
+//    k-d order (splits at leaf-aligned medians); each node then has a 32-ary
+//    box hierarchy over 32-member leaves, searched one query per warp for
+//    nearest neighbours and friends.  Children above SMALL_N stay on the big
+//    path, smaller children join the small-node queue;
 //  * small nodes (<= SMALL_N members): one CTA loads the node into shared
 //    memory and builds its whole subtree there (moments, nearest neighbours,
 //    exact k-th select, union-find, children, recursion with an explicit
-//    stack), as a persistent work queue over all small nodes; tiny nodes it
-//    meets (roots or children) go to the tiny queue;
-//  * big nodes: processed level by level by tiles of 256 members spread over
-//    the whole GPU, with per-node accumulators and histograms in global
-//    memory; children above SMALL_N stay on the big path, smaller children
-//    join the small-node queue.
+//    stack), as a persistent work queue; a second instance with 128 threads
+//    and MID_N-member shared arrays takes the subtrees of at most MID_N
+//    members, which the first forwards to it;
+//  * tiny nodes (<= TINY_N = 32 members): one warp holds the node in
+//    registers, a member per lane, and builds its whole subtree with warp
+//    shuffles and votes, eight subtrees per CTA at a time; the middle
+//    instance forwards them here.
 //
 // Exactness: means and dispersions come from exact fixed-point integer sums;
 // nearest-neighbour and link tests run in float32 against a band of 2^-20
