@@ -1385,16 +1385,20 @@ __global__ void __launch_bounds__(W_WARPS * 32) k_bvh_nn_sample(LevelBufs L, Nod
 // one candidate pair: bit 0 set when it is within l (decided in float64
 // inside the band), bit 1 set for a pair within 1e-6 (relative) of l but not
 // at it
-__device__ __forceinline__ int pair_test(const LinkLim &lm, const Metric6 &met, float4 pa, float4 va, float4 pb,
-                                         float4 vb)
+// (The float64 metric and l^2 are read from memory on the rare band path
+// only, which keeps them out of the search kernel's registers.)
+__device__ __forceinline__ int pair_test(const LinkLim &lm, const Metric6 &met, const Metric6 *met64,
+                                         const double *l2p, float4 pa, float4 va, float4 pb, float4 vb)
 {
     const float d2 = d2_32(pa, va, pb, vb, met);
     if (d2 > lm.part) return 0;
     if (d2 <= lm.lo) return 1;
     if (d2 <= lm.hi || (d2 >= lm.tlo && d2 <= lm.thi)) {
-        const double e64 = d2_64(pa, va, pb, vb, met);
-        const int tie = (lm.l2 > 0 && e64 != lm.l2 && fabs(sqrt(e64) - lm.l) <= 1e-6 * lm.l) ? 2 : 0;
-        return (e64 <= lm.l2 ? 1 : 0) | tie;
+        const Metric6 m = *met64;
+        const double l2 = *l2p, l = sqrt(l2);
+        const double e64 = d2_64(pa, va, pb, vb, m);
+        const int tie = (l2 > 0 && e64 != l2 && fabs(sqrt(e64) - l) <= 1e-6 * l) ? 2 : 0;
+        return (e64 <= l2 ? 1 : 0) | tie;
     }
     return 0;
 }
@@ -1462,7 +1466,8 @@ constexpr int LK_BATCH = 2;    // leaves scanned together
 // which it scans LK_BATCH leaves at a time (one member per lane and leaf), so
 // several independent loads are in flight per warp.
 __device__ __forceinline__ int w32_link(const BvhView &V, const MemberStore &M, const float *D, int n,
-                                        int q, float4 pq, float4 vq, const Metric6 &met, const LinkLim &lm, int own,
+                                        int q, float4 pq, float4 vq, const Metric6 &met, const Metric6 *met64,
+                                        const double *l2p, const LinkLim &lm, int own,
                                         int *parent, int first, int *si, int *lf, int &rq, rs_dev_status *st,
                                         int node)
 {
@@ -1526,7 +1531,7 @@ __device__ __forceinline__ int w32_link(const BvhView &V, const MemberStore &M, 
 #pragma unroll
             for (int u = 0; u < LK_BATCH; u++) {
                 if (dd[u] <= lm.part) {
-                    const int r = pair_test(lm, met, pq, vq, pp[u], vv[u]);
+                    const int r = pair_test(lm, met, met64, l2p, pq, vq, pp[u], vv[u]);
                     tie += r >> 1;
                     if (r & 1) nr = min(nr, join_friend(parent, first + q, first + mm[u], rq, st));
                 }
@@ -1540,7 +1545,7 @@ __device__ __forceinline__ int w32_link(const BvhView &V, const MemberStore &M, 
 // friends-of-friends at l, one warp per leaf of 32 consecutive members, pairs
 // with the candidate after the query in the node's member order; only
 // members with a neighbour within reach take part
-__global__ void __launch_bounds__(TQ, 4) k_bvh_link(LevelBufs L, NodeArrays nd, const int64_t *box_base,
+__global__ void __launch_bounds__(TQ, 5) k_bvh_link(LevelBufs L, NodeArrays nd, const int64_t *box_base,
                                                  BoxStore B, MemberStore MS, const float *dnn, int *parent,
                                                  rs_dev_status *st)
 {
@@ -1550,7 +1555,11 @@ __global__ void __launch_bounds__(TQ, 4) k_bvh_link(LevelBufs L, NodeArrays nd, 
     const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x] + 32 * w;
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
     if (q0 >= n) return;
-    const Metric6 met = L.met[k];
+    Metric6 met;  // float32 factors only; the float64 ones are read where needed
+    met.ax = L.met[k].ax;
+    met.av = L.met[k].av;
+    const Metric6 *met64 = L.met + k;
+    const double *l2p = L.l2 + k;
     const LinkLim lm = link_lim(L.l2[k]);
     const MemberStore M = mem_shift(MS, first);
     const float *D = dnn + first;
@@ -1575,12 +1584,13 @@ __global__ void __launch_bounds__(TQ, 4) k_bvh_link(LevelBufs L, NodeArrays nd, 
         // pairs inside the own leaf, lane > j
         int nr = 0x7fffffff;
         if (lane > j && act) {
-            const int r = pair_test(lm, met, pq, vq, po, vo);
+            const int r = pair_test(lm, met, met64, l2p, pq, vq, po, vo);
             tie += r >> 1;
             if (r & 1) nr = join_friend(parent, first + q, first + mo, rq, st);
         }
         rq = min(rq, (int)__reduce_min_sync(FULLW, (unsigned)nr));
-        tie += w32_link(V, M, D, n, q, pq, vq, met, lm, own, parent, first, si_s[w], lf_s[w], rq, st, node);
+        tie += w32_link(V, M, D, n, q, pq, vq, met, met64, l2p, lm, own, parent, first, si_s[w], lf_s[w], rq, st,
+                        node);
     }
     tie = warp_sum(tie);
     if (lane == 0 && tie) atomicAdd(&L.tie[k], tie);
