@@ -117,7 +117,7 @@ rs_status rs_group_sort(rs_ctx *ctx, const int32_t *labels, int64_t n, int32_t m
  * It writes the same labels as rs_fof3d (device pointers pos and labels,
  * owned by the caller; work enqueued on cuda_stream, NULL = legacy default
  * stream) and synchronises that stream before returning.  Every temporary
- * lives in one fixed scratch array of about 9 MB inside the library image,
+ * lives in one fixed scratch array of about 10 MB inside the library image,
  * which every GPU that loads the library holds until the process exits.
  * Limits: at most 65536 particles, and a neighbour table of at most 2^20
  * cells (about 7 linking lengths times 2^(20/3) per box side); beyond either,
