@@ -61,6 +61,11 @@ def _load():
     lib.or_set_kd_threshold.argtypes = [C.c_int]
     lib.or_refine.argtypes = [P, P, i64, f64, P, P, i64, f64, i32, C.POINTER(C.c_int)]
     lib.or_refine.restype = P
+    lib.or_refine_sampled.argtypes = [P, P, i64, f64, P, P, i64, f64, i32, i64, C.c_uint64, C.POINTER(C.c_int)]
+    lib.or_refine_sampled.restype = P
+    lib.or_sample_key.argtypes = [C.c_uint64, i64]
+    lib.or_sample_key.restype = C.c_uint64
+    lib.or_sample_keys.argtypes = [C.c_uint64, i64, i64, P]
     lib.or_tree_n_nodes.argtypes = [P]
     lib.or_tree_n_nodes.restype = i64
     lib.or_tree_n_members.argtypes = [P]
@@ -226,10 +231,26 @@ class Tree:
             pass
 
 
+def sample_key(seed: int, i: int) -> int:
+    """Sec. 3.2 subset draws: the SplitMix64 key of particle i (the (i+1)-th
+    output of the stream whose state starts at `seed`)."""
+    return int(_load().or_sample_key(int(seed) & (2 ** 64 - 1), int(i)))
+
+
+def sample_keys(seed: int, first: int, count: int) -> np.ndarray:
+    """:func:`sample_key` of particles first .. first+count-1 (uint64)."""
+    out = np.empty(count, np.uint64)
+    _load().or_sample_keys(int(seed) & (2 ** 64 - 1), int(first), int(count), _ptr(out))
+    return out
+
+
 def refine(pos, vel, box: float, members, offsets, f: float = 0.7, min_n: int = 10,
-           kd_threshold: int = 1024) -> Tree:
+           kd_threshold: int = 1024, sub_n: int = 0, sub_seed: int = 0) -> Tree:
     """Sec. 3.2: phase-space FOF hierarchy of every group (members/offsets
-    as returned by :func:`groups_from_labels`)."""
+    as returned by :func:`groups_from_labels`).  With sub_n > 0, a node of
+    more than sub_n members takes its linking length from the nearest-
+    neighbour distances of the sub_n members with the smallest
+    :func:`sample_key` values (the paper's random 10,000-member subset)."""
     lib = _load()
     pos = _f32(pos)
     vel = _f32(vel)
@@ -237,8 +258,9 @@ def refine(pos, vel, box: float, members, offsets, f: float = 0.7, min_n: int = 
     offsets = np.ascontiguousarray(offsets, np.int64)
     lib.or_set_kd_threshold(int(kd_threshold))
     st = C.c_int(0)
-    h = lib.or_refine(_ptr(pos), _ptr(vel), pos.shape[0], float(box), _ptr(members), _ptr(offsets),
-                      offsets.shape[0] - 1, float(f), int(min_n), C.byref(st))
+    h = lib.or_refine_sampled(_ptr(pos), _ptr(vel), pos.shape[0], float(box), _ptr(members), _ptr(offsets),
+                              offsets.shape[0] - 1, float(f), int(min_n), int(sub_n),
+                              int(sub_seed) & (2 ** 64 - 1), C.byref(st))
     if not h:
         raise RuntimeError(f"or_refine failed with status {st.value}")
     if st.value:

@@ -13,6 +13,10 @@
  *   or_fof3d         3D friends-of-friends, periodic minimum image (Sec. 3.1)
  *   or_grid_*        the same graph queried one component at a time (Sec. 3.1)
  *   or_refine        per-group phase-space hierarchy (Sec. 3.2, Eq. 1)
+ *   or_refine_sampled  the same, with the linking length of a node above a
+ *                    size limit taken from the nearest-neighbour distances
+ *                    of a random subset of its members (Sec. 3.2)
+ *   or_sample_key    the counter-based generator that draws those subsets
  *   or_assign        seeds, seed merge (Eq. 2), r_dyn,vir (Eq. 4) and the
  *                    hierarchical particle assignment with Eq. 3 (Sec. 3.3)
  *
@@ -636,6 +640,8 @@ struct or_tree {
     int64_t n_total;
     double box, f;
     int32_t min_n;
+    int64_t sub_n;      /* nodes above this size use a subset of sub_n members for l (0: never) */
+    uint64_t sub_seed;  /* seed of the subset keys */
     int32_t *mem;       /* member particle indices, groups back to back */
     int64_t n_mem;
     or_node *nodes;
@@ -679,6 +685,61 @@ static int cmp_sort_rec(const void *a, const void *b)
     return (x->pidx > y->pidx) - (x->pidx < y->pidx);
 }
 
+/* ---- random subsets for the linking length (Sec. 3.2) -------------------
+ * Nodes with more members than a limit s take their linking length from the
+ * nearest-neighbour distances of s randomly chosen members instead of all of
+ * them.  The randomness is SplitMix64 (Steele, Lea & Flood, "Fast splittable
+ * pseudorandom number generators", OOPSLA 2014) used as a counter-based
+ * generator: particle i gets the (i+1)-th output of the stream whose state
+ * starts at the seed, i.e. the finaliser applied to seed + (i+1)*gamma.  The
+ * finaliser is a bijection of 64-bit words and gamma is odd, so distinct
+ * particles get distinct keys; a node's subset is its s members with the
+ * smallest keys, which is a uniformly random s-subset. */
+#define SM64_GAMMA 0x9e3779b97f4a7c15ULL
+
+static uint64_t sm64_finalise(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+uint64_t or_sample_key(uint64_t seed, int64_t i) { return sm64_finalise(seed + (uint64_t)(i + 1) * SM64_GAMMA); }
+
+/* keys of particles first .. first+count-1 */
+void or_sample_keys(uint64_t seed, int64_t first, int64_t count, uint64_t *out)
+{
+    for (int64_t i = 0; i < count; i++) out[i] = or_sample_key(seed, first + i);
+}
+
+typedef struct {
+    uint64_t key;
+    int64_t slot;
+} key_slot;
+
+static int cmp_key_slot(const void *a, const void *b)
+{
+    const key_slot *x = (const key_slot *)a, *y = (const key_slot *)b;
+    return (x->key > y->key) - (x->key < y->key);
+}
+
+/* Marks in `in` (0/1 per slot) the s members of mem[0..n) with the smallest
+ * keys. */
+static int sample_subset(const int32_t *mem, int64_t n, int64_t s, uint64_t seed, unsigned char *in)
+{
+    key_slot *ks = (key_slot *)malloc(sizeof(key_slot) * (size_t)n);
+    if (!ks) return OR_ERR_OOM;
+    for (int64_t a = 0; a < n; a++) {
+        ks[a].key = or_sample_key(seed, mem[a]);
+        ks[a].slot = a;
+        in[a] = 0;
+    }
+    qsort(ks, (size_t)n, sizeof(key_slot), cmp_key_slot);
+    for (int64_t a = 0; a < s && a < n; a++) in[ks[a].slot] = 1;
+    free(ks);
+    return OR_OK;
+}
+
 /* Refines one node (Sec. 3.2) and recurses into its children. */
 static int refine_node(or_tree *t, int64_t id)
 {
@@ -696,12 +757,24 @@ static int refine_node(or_tree *t, int64_t id)
     nd.sigv = m.sigv;
     grp_t g = {t->pos, t->vel, mem, t->box, m.sigx, m.sigv};
 
-    /* nearest-neighbour distance of every member under Eq. 1 */
+    /* nearest-neighbour distance under Eq. 1 of every member, or of the
+     * random subset's members when the node is above the subset size (the
+     * neighbour is still searched among all members); the others get -1 */
     double *dnn2 = (double *)malloc(sizeof(double) * (size_t)n);
     double *u = NULL;
     kdtree kd;
     int use_kd = n > g_kd_threshold;
     if (!dnn2) return OR_ERR_OOM;
+    const int sampled = t->sub_n > 0 && n > t->sub_n;
+    const int64_t n_eff = sampled ? t->sub_n : n;
+    unsigned char *in = (unsigned char *)malloc((size_t)n);
+    if (!in) return OR_ERR_OOM;
+    if (sampled) {
+        st = sample_subset(mem, n, t->sub_n, t->sub_seed, in);
+        if (st) return st;
+    } else {
+        memset(in, 1, (size_t)n);
+    }
     if (use_kd) {
         int32_t ref = mem[0];
         for (int64_t a = 1; a < n; a++)
@@ -719,12 +792,20 @@ static int refine_node(or_tree *t, int64_t id)
         if (kd_build(&kd, u, n)) return OR_ERR_OOM;
         for (int64_t a = 0; a < n; a++) {
             double best = INFINITY;
+            if (!in[a]) {
+                dnn2[a] = -1.0;
+                continue;
+            }
             kd_nn_rec(&kd, &g, 0, (int32_t)a, &best);
             dnn2[a] = best;
         }
     } else {
         for (int64_t a = 0; a < n; a++) {
             double best = INFINITY;
+            if (!in[a]) {
+                dnn2[a] = -1.0;
+                continue;
+            }
             for (int64_t b = 0; b < n; b++) {
                 if (b == a) continue;
                 double d2 = gdist2(&g, (int32_t)a, (int32_t)b);
@@ -736,14 +817,18 @@ static int refine_node(or_tree *t, int64_t id)
 
     /* linking length: the k-th smallest nearest-neighbour distance with
      * k = ceil(f n), so that at least a fraction f of the members have a
-     * friend within it (reading of "a constant fraction f ... are linked") */
-    int64_t k = (int64_t)ceil(t->f * (double)n);
+     * friend within it (reading of "a constant fraction f ... are linked");
+     * over the subset, with n its size, when the node is sampled */
+    int64_t k = (int64_t)ceil(t->f * (double)n_eff);
     if (k < 1) k = 1;
-    if (k > n) k = n;
-    double *srt = (double *)malloc(sizeof(double) * (size_t)n);
+    if (k > n_eff) k = n_eff;
+    double *srt = (double *)malloc(sizeof(double) * (size_t)n_eff);
     if (!srt) return OR_ERR_OOM;
-    memcpy(srt, dnn2, sizeof(double) * (size_t)n);
-    qsort(srt, (size_t)n, sizeof(double), cmp_f64);
+    int64_t ns = 0;
+    for (int64_t a = 0; a < n; a++)
+        if (in[a]) srt[ns++] = dnn2[a];
+    free(in);
+    qsort(srt, (size_t)ns, sizeof(double), cmp_f64);
     double l2 = srt[k - 1];
     free(srt);
     double l = sqrt(l2);
@@ -877,12 +962,17 @@ static int refine_node(or_tree *t, int64_t id)
  * members[group_offsets[g] .. group_offsets[g+1]).  Groups with fewer than
  * min_n members are not refined (reading: the recursion floor applies to the
  * 3D groups too).  Recursion stops at nodes without a subgroup of at least
- * min_n members; those nodes are the seed halos (Sec. 3.3). */
-or_tree *or_refine(const float *pos, const float *vel, int64_t n_total, double box, const int32_t *members,
-                   const int64_t *group_offsets, int64_t n_groups, double f, int32_t min_n, int *status)
+ * min_n members; those nodes are the seed halos (Sec. 3.3).  With sub_n > 0
+ * a node of more than sub_n members takes its linking length from the
+ * nearest-neighbour distances of sub_n of its members, drawn with the keys of
+ * or_sample_key(sub_seed, .), and k = ceil(f sub_n) (Sec. 3.2: above 10,000
+ * members the paper computes them for a random 10,000-member subset). */
+or_tree *or_refine_sampled(const float *pos, const float *vel, int64_t n_total, double box, const int32_t *members,
+                           const int64_t *group_offsets, int64_t n_groups, double f, int32_t min_n, int64_t sub_n,
+                           uint64_t sub_seed, int *status)
 {
     *status = OR_ERR_ARG;
-    if (!(box > 0) || !(f > 0 && f < 1) || min_n < 2 || n_groups < 0) return NULL;
+    if (!(box > 0) || !(f > 0 && f < 1) || min_n < 2 || n_groups < 0 || sub_n < 0) return NULL;
     or_tree *t = (or_tree *)calloc(1, sizeof(or_tree));
     if (!t) {
         *status = OR_ERR_OOM;
@@ -894,6 +984,8 @@ or_tree *or_refine(const float *pos, const float *vel, int64_t n_total, double b
     t->box = box;
     t->f = f;
     t->min_n = min_n;
+    t->sub_n = sub_n;
+    t->sub_seed = sub_seed;
     t->n_mem = group_offsets[n_groups] - group_offsets[0];
     t->mem = (int32_t *)malloc(sizeof(int32_t) * (size_t)(t->n_mem > 0 ? t->n_mem : 1));
     if (!t->mem) {
@@ -929,6 +1021,13 @@ or_tree *or_refine(const float *pos, const float *vel, int64_t n_total, double b
     }
     *status = OR_OK;
     return t;
+}
+
+/* Every member's nearest-neighbour distance enters the linking length. */
+or_tree *or_refine(const float *pos, const float *vel, int64_t n_total, double box, const int32_t *members,
+                   const int64_t *group_offsets, int64_t n_groups, double f, int32_t min_n, int *status)
+{
+    return or_refine_sampled(pos, vel, n_total, box, members, group_offsets, n_groups, f, min_n, 0, 0, status);
 }
 
 int64_t or_tree_n_nodes(const or_tree *t) { return t->n_nodes; }
