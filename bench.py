@@ -141,7 +141,7 @@ def sub_cube(cat, frac_side: float):
     return cat.pos[m].copy(), cat.vel[m].copy()
 
 
-def time_oracle_sample(cat, frac_side: float):
+def time_oracle_sample(cat, frac_side: float, nn_subset: int = 0, nn_seed: int = 0):
     import oracle
     pos, vel = sub_cube(cat, frac_side)
     # the linking length of the full catalogue
@@ -149,7 +149,7 @@ def time_oracle_sample(cat, frac_side: float):
     t0 = time.perf_counter()
     lab, _, _ = oracle.fof3d(pos, cat.box, l=l)
     mem, off = oracle.groups_from_labels(lab, 10)
-    tree = oracle.refine(pos, vel, cat.box, mem, off, 0.7, 10)
+    tree = oracle.refine(pos, vel, cat.box, mem, off, 0.7, 10, sub_n=nn_subset, sub_seed=nn_seed)
     oracle.assign(tree, len(pos), cat.box, 360.0, cat.n / cat.box ** 3)
     return len(pos), time.perf_counter() - t0
 
@@ -158,10 +158,10 @@ def reference_arm(args, cat, cfg_json):
     """The oracle, as it stands, on host cores: each step one bounded sample."""
     side = args.ref_side
     for _ in range(args.warmup):
-        time_oracle_sample(cat, side)
+        time_oracle_sample(cat, side, args.nn_subset, args.nn_seed)
     tot_p, tot_t = 0, 0.0
     for _ in range(args.steps):
-        p, t = time_oracle_sample(cat, side)
+        p, t = time_oracle_sample(cat, side, args.nn_subset, args.nn_seed)
         tot_p += p
         tot_t += t
     v = tot_p / tot_t
@@ -221,6 +221,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nn-subset", type=int, default=0,
+                    help="nodes above this size take l from a random subset of this size (Sec. 3.2; 0: exact)")
+    ap.add_argument("--nn-seed", type=int, default=11104372, help="seed of those subsets")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-side", type=float, default=1.0 / 6.0, help="sub-cube side for the CPU baseline")
@@ -233,6 +236,9 @@ def main():
     cfg_json = {"workload": WORKLOADS[args.config], "name": args.config, "particles": cfg["n"], "box": cfg["box"],
                 "b": 0.28, "f": 0.7, "min_n": 10, "parallelism": "replicas" if world > 1 else "single",
                 "l2": "inputs larger than L2 (pos+vel 24 B/particle)"}
+    if args.nn_subset:
+        cfg_json["nn_subset"] = args.nn_subset
+        cfg_json["nn_seed"] = args.nn_seed
 
     if args.impl == "reference":
         if rank != 0:
@@ -253,7 +259,7 @@ def main():
     pos = torch.from_numpy(cat.pos).cuda()
     vel = torch.from_numpy(cat.vel).cuda()
     halo = torch.empty(n, dtype=torch.int32, device="cuda")
-    p = rsgpu.params()
+    p = rsgpu.params(nn_subset=args.nn_subset, nn_seed=args.nn_seed)
 
     def step():
         _, _, st = rsgpu.rs_find_halos(ctx, pos, vel, cat.box, p, halo_id=halo)
@@ -342,7 +348,7 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline:
-        npart, t = time_oracle_sample(cat, args.cpu_side)
+        npart, t = time_oracle_sample(cat, args.cpu_side, args.nn_subset, args.nn_seed)
         cpu = {"value": npart / t, "unit": "particles/s", "cores": 1, "kind": "oracle",
                "sample": f"{npart} particles in the sub-cube [0, {args.cpu_side:.4g} L)^3 of the workload: "
                          f"3D FOF + refinement + assignment, float64 C oracle, single thread, {t:.1f} s"}

@@ -7,8 +7,10 @@
  *   rs_fof3d       3D friends-of-friends over the box                Sec. 3.1
  *   rs_group_sort  groups of at least min_n particles as a CSR list  Sec. 3.1, App. A
  *   rs_refine6d    phase-space FOF hierarchy inside every group      Sec. 3.2, Eq. 1
+ *   rs_refine6d_sampled  the same with subset linking lengths        Sec. 3.2
  *   rs_assign      seeds, seed merge and particle assignment         Sec. 3.3, Eqs. 2-4
- *   rs_find_halos  the four calls above in sequence, with host or device buffers
+ *   rs_find_halos  rs_fof3d, rs_group_sort, rs_refine6d(_sampled) and rs_assign
+ *                  in sequence, with host or device buffers
  *
  * Conventions shared by every entry point
  * ----------------------------------------
@@ -61,10 +63,15 @@ typedef struct {
     double delta_vir;    /* rho_vir / rho_background for r_dyn,vir (360) */
     double nbar;         /* background number density; <= 0 means n / box^3 */
     double merge_thresh; /* seeds merge below this Eq. 2 separation (10 sqrt 2) */
+    int64_t nn_subset;   /* 0: every member's nearest neighbour sets a node's linking length;
+                            else nodes above this many members use a random subset of this
+                            size (the paper uses 10,000, Sec. 3.2); 0 or in [1024, 2^31) */
+    uint64_t nn_seed;    /* seed of that subset (see rs_refine6d_sampled) */
 } rs_params;
 
 /* Fills p with the paper's defaults: b = 0.28, f = 0.7, min_n = 10,
- * delta_vir = 360, nbar = 0 (derived), merge_thresh = 10 sqrt 2. */
+ * delta_vir = 360, nbar = 0 (derived), merge_thresh = 10 sqrt 2, and the
+ * exact linking length (nn_subset = 0, nn_seed = 0). */
 void rs_params_default(rs_params *p);
 
 /* Creates a context bound to a CUDA stream (a cudaStream_t cast to void*;
@@ -150,6 +157,23 @@ rs_status rs_fof3d_static(const float *pos, int32_t stride, int64_t n, double bo
 rs_status rs_refine6d(rs_ctx *ctx, const float *pos, const float *vel, int32_t stride, int64_t n, double box,
                       const int32_t *perm, const int64_t *group_offsets, int64_t n_groups, double f,
                       int32_t min_n, rs_tree **out);
+
+/* rs_refine6d with the paper's subsampled linking length (Sec. 3.2: in
+ * groups above 10,000 particles the nearest neighbours of a random 10,000-
+ * particle subset set the linking length).  A node with more than subset_n
+ * members computes the nearest-neighbour distance (among all its members)
+ * of subset_n of them only, and its linking length is the k-th smallest of
+ * those with k = ceil(f subset_n); linking still uses every pair.  The subset
+ * is the subset_n members with the smallest keys, particle i's key being the
+ * SplitMix64 output (Steele, Lea & Flood 2014) for the counter
+ * subset_seed + (i+1) * 0x9e3779b97f4a7c15: z ^= z >> 30; z *= 0xbf58476d1ce4e5b9;
+ * z ^= z >> 27; z *= 0x94d049bb133111eb; z ^= z >> 31 (all mod 2^64).  Keys
+ * are distinct, so the subset is unique and the result deterministic.
+ * subset_n = 0 is rs_refine6d.  RS_ERR_INVALID_ARG unless subset_n is 0 or in
+ * [1024, 2^31).  Everything else as rs_refine6d. */
+rs_status rs_refine6d_sampled(rs_ctx *ctx, const float *pos, const float *vel, int32_t stride, int64_t n,
+                              double box, const int32_t *perm, const int64_t *group_offsets, int64_t n_groups,
+                              double f, int32_t min_n, int64_t subset_n, uint64_t subset_seed, rs_tree **out);
 
 /* Host scalars of a tree: node count, number of levels (max level + 1),
  * seed (leaf) count, tie-band pairs over all nodes, member count (the sum of

@@ -328,11 +328,13 @@ def node_dnn(pos, vel, mem, box: float, f: float = 0.7):
     return dnn2, l2, dict(sigx=sig[0], sigv=sig[1], xbar=sig[2:5].copy(), vbar=sig[5:8].copy())
 
 
-def run_all(pos, vel, box: float, b: float = 0.28, f: float = 0.7, min_n: int = 10, assign_too: bool = True):
-    """The whole path on one catalogue: 3D FOF, refinement, assignment."""
+def run_all(pos, vel, box: float, b: float = 0.28, f: float = 0.7, min_n: int = 10, assign_too: bool = True,
+            sub_n: int = 0, sub_seed: int = 0):
+    """The whole path on one catalogue: 3D FOF, refinement (with subset
+    linking lengths above sub_n members when sub_n > 0), assignment."""
     labels, l, tie3 = fof3d(pos, box, b)
     members, offsets = groups_from_labels(labels, min_n)
-    tree = refine(pos, vel, box, members, offsets, f, min_n)
+    tree = refine(pos, vel, box, members, offsets, f, min_n, sub_n=sub_n, sub_seed=sub_seed)
     out = dict(labels=labels, l=l, tie3=tie3, members=members, offsets=offsets, tree=tree)
     if assign_too:
         hid, halos = assign(tree, np.asarray(pos).reshape(-1, 3).shape[0], box)

@@ -35,7 +35,8 @@ extern "C" rs_status rs_find_halos(rs_ctx *ctx, const float *pos, const float *v
     int64_t G = 0, M = 0;
     RS_TRY(rs_group_sort(ctx, labels, n, params->min_n, perm, offsets, ocap, &G, &M));
     rs_tree *tree = nullptr;
-    RS_TRY(rs_refine6d(ctx, dpos, dvel, stride, n, box, perm, offsets, G, params->f, params->min_n, &tree));
+    RS_TRY(rs_refine6d_sampled(ctx, dpos, dvel, stride, n, box, perm, offsets, G, params->f, params->min_n,
+                               params->nn_subset, params->nn_seed, &tree));
     int64_t H = 0;
     rs_status s = rs_assign(ctx, tree, dpos, dvel, stride, n, box, params, hid, &H);
     if (s == RS_OK) {

@@ -14,6 +14,8 @@ extern "C" void rs_params_default(rs_params *p)
     p->delta_vir = 360.0;
     p->nbar = 0.0;
     p->merge_thresh = 10.0 * std::sqrt(2.0);
+    p->nn_subset = 0;
+    p->nn_seed = 0;
 }
 
 extern "C" double rs_linking_length(int64_t n, double box, double b)

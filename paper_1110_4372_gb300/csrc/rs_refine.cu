@@ -32,6 +32,12 @@
 // float64 k-th smallest nearest-neighbour distance: the float32 k-th value
 // brackets it, and only the members whose float32 distance lies within twice
 // the band of it are re-evaluated in float64 and ranked.
+//
+// Optionally (subset size s > 0) a big node of more than s members takes its
+// linking length from the nearest-neighbour distances of a random s-member
+// subset only (Sec. 3.2, the paper's s = 10,000): the subset is found by a
+// radix select on per-particle SplitMix64 keys and searched one warp per
+// member; the other members skip the nearest-neighbour search.
 #include <cmath>
 #include <cstring>
 
@@ -802,6 +808,8 @@ struct LevelBufs {
     double *band_val;
     double *l2;              // per rank
     int *tie;                // per rank
+    unsigned *sub_t;         // per rank: subset key threshold, high and low words (2 entries)
+    int *sub_cnt;            // per rank: members drawn into the subset
 };
 
 __global__ void k_lvl_prep(const int *list, int K, NodeArrays nd, int64_t *tiles, int64_t *segc,
@@ -1382,6 +1390,34 @@ __global__ void __launch_bounds__(W_WARPS * 32) k_bvh_nn_sample(LevelBufs L, Nod
     if (lane == 0) out[soff[k] + s] = best;
 }
 
+// nearest-neighbour distance of listed members (rank, member), one warp
+// each, unbounded; the result goes to the member's own slot
+__global__ void __launch_bounds__(W_WARPS * 32) k_bvh_nn_list(LevelBufs L, NodeArrays nd, const int64_t *box_base,
+                                                              BoxStore B, MemberStore MS, const int2 *qlist,
+                                                              const int *qlen, int cap, float *dnn,
+                                                              rs_dev_status *st)
+{
+    __shared__ int si_s[W_WARPS][W_STACK];
+    __shared__ float sd_s[W_WARPS][W_STACK];
+    const int w = warp_id(), lane = lane_id();
+    const int64_t s = (int64_t)blockIdx.x * W_WARPS + w;
+    if (s >= min(*qlen, cap)) return;
+    const int2 e = qlist[s];
+    const int k = e.x, q = e.y;
+    const int node = L.list[k], first = nd.first[node], n = nd.count[node];
+    const Metric6 met = L.met[k];
+    BvhView V;
+    bvh_view(V, B, box_base[k], n);
+    const MemberStore M = mem_shift(MS, first);
+    float4 pq, vq, pm = make_float4(0, 0, 0, 0), vm = pm;
+    mem_get(M, q, pq, vq);
+    const int own = q / BVH_LEAF, m = own * BVH_LEAF + lane;
+    if (m < n) mem_get(M, m, pm, vm);
+    const float d = (m < n && m != q) ? d2_32(pq, vq, pm, vm, met) : INFINITY;
+    const float best = w32_nn(V, M, n, q, pq, vq, met, wmin(d), 0.f, own, si_s[w], sd_s[w], st, node);
+    if (lane == 0) dnn[first + q] = best;
+}
+
 // one candidate pair: bit 0 set when it is within l (decided in float64
 // inside the band), bit 1 set for a pair within 1e-6 (relative) of l but not
 // at it
@@ -1608,12 +1644,14 @@ __global__ void __launch_bounds__(TQ, 5) k_bvh_link(LevelBufs L, NodeArrays nd, 
 constexpr int SMP_MAX = 1024;       // sample size per node
 constexpr int SMP_MIN_NODE = 4096;  // smaller nodes are searched without a bracket
 
-__global__ void k_smp_prep(const int *list, int K, NodeArrays nd, int64_t *ns)
+// (nodes that draw a member subset for the linking length search only the
+// subset, without a bracket)
+__global__ void k_smp_prep(const int *list, int K, NodeArrays nd, int64_t *ns, int sub_n)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
     const int n = nd.count[list[k]];
-    ns[k] = n > SMP_MIN_NODE ? SMP_MAX : 0;
+    ns[k] = (n > SMP_MIN_NODE && !(sub_n > 0 && n > sub_n)) ? SMP_MAX : 0;
 }
 
 // full-search warp jobs: every 32 consecutive members of every node
@@ -1631,11 +1669,14 @@ __global__ void k_full_jobs(const int *list, int K, NodeArrays nd, const int64_t
     }
 }
 
-__global__ void k_full_prep(const int *list, int K, NodeArrays nd, int64_t *nw)
+// warp jobs of 32 members per node; none for a node above the subset size
+// (sub_n > 0), whose subset members are searched one by one instead
+__global__ void k_full_prep(const int *list, int K, NodeArrays nd, int64_t *nw, int sub_n)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
-    nw[k] = ceil_div(nd.count[list[k]], 32);
+    const int n = nd.count[list[k]];
+    nw[k] = (sub_n > 0 && n > sub_n) ? 0 : ceil_div(n, 32);
 }
 
 // bracket of the search from the sample: the radius R2 is the sample's
@@ -1923,11 +1964,125 @@ __device__ __forceinline__ void sel_digit(unsigned bits, int pass, unsigned &dig
     }
 }
 
-__global__ void k_lvl_initk(LevelBufs L, NodeArrays nd, double f)
+// ---- random member subsets for the linking length (Sec. 3.2) ----
+// Above sub_n members a node takes its linking length from the nearest-
+// neighbour distances of sub_n randomly drawn members (their neighbours are
+// still searched among all members).  Each particle carries a 64-bit key from
+// the SplitMix64 generator (Steele, Lea & Flood 2014) used counter-based:
+// particle i gets the finaliser of seed + (i+1)*gamma.  The finaliser is a
+// bijection, so keys are distinct and the subset -- the sub_n members with
+// the smallest keys -- is well defined; it is found by a radix select on the
+// key's high word, then on its low word among the members that tie on the
+// high word.  Members outside the subset get a nearest-neighbour value of -1,
+// which the select skips and the link treats as "may have a friend".
+__device__ __forceinline__ unsigned long long subset_key(unsigned long long seed, int i)
+{
+    unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_sub_init(LevelBufs L, NodeArrays nd, int sub_n)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= L.K) return;
     const int n = nd.count[L.list[k]];
+    L.sel_krem[k] = n > sub_n ? sub_n : 1;
+    L.sel_prefix[k] = 0u;
+    L.sub_cnt[k] = 0;
+}
+
+// one radix-select pass over the keys of the members of nodes above sub_n:
+// stage 0 selects on the high word, stage 1 on the low word of the members
+// whose high word equals the stage-0 result
+__global__ void __launch_bounds__(TQ) k_sub_hist(LevelBufs L, NodeArrays nd, const int *widx,
+                                                 unsigned long long seed, int sub_n, int stage, int pass)
+{
+    __shared__ unsigned h[2048];
+    const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x];
+    const int node = L.list[k], first = nd.first[node], n = nd.count[node];
+    if (n <= sub_n) return;  // the whole tile belongs to one node
+    for (int i = threadIdx.x; i < 2048; i += TQ) h[i] = 0;
+    __syncthreads();
+    const int q = q0 + threadIdx.x;
+    if (q < n) {
+        const unsigned long long key = subset_key(seed, widx[first + q]);
+        const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+        if (stage == 0 || hi == L.sub_t[2 * k]) {
+            const unsigned bits = stage == 0 ? hi : lo;
+            unsigned digit, mask;
+            sel_digit(bits, pass, digit, mask);
+            if ((bits & mask) == (L.sel_prefix[k] & mask)) atomicAdd(&h[digit], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2048; i += TQ)
+        if (h[i]) atomicAdd(&L.hist[(int64_t)k * 2048 + i], h[i]);
+}
+
+// stores a stage's selected word; the rank still to select carries over
+__global__ void k_sub_stage(LevelBufs L, int stage)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.K) return;
+    L.sub_t[2 * k + stage] = L.sel_prefix[k];
+    L.sel_prefix[k] = 0u;
+}
+
+// members of the subset go to the query list (rank, member); the others get
+// the "outside the subset" value
+__global__ void __launch_bounds__(TQ) k_sub_mark(LevelBufs L, NodeArrays nd, const int *widx,
+                                                 unsigned long long seed, int sub_n, float *dnn, int2 *qlist,
+                                                 int *qlen, int cap, rs_dev_status *st)
+{
+    const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x];
+    const int node = L.list[k], first = nd.first[node], n = nd.count[node];
+    if (n <= sub_n) return;
+    const int q = q0 + threadIdx.x;
+    bool in = false;
+    if (q < n) {
+        const unsigned long long key = subset_key(seed, widx[first + q]);
+        const unsigned long long t = ((unsigned long long)L.sub_t[2 * k] << 32) | L.sub_t[2 * k + 1];
+        in = key <= t;
+        if (!in) dnn[first + q] = -1.0f;
+    }
+    const unsigned m = __ballot_sync(FULLW, in);
+    if (!m) return;
+    const int lane = lane_id();
+    int base = 0;
+    if (lane == __ffs(m) - 1) {
+        base = atomicAdd(qlen, __popc(m));
+        atomicAdd(&L.sub_cnt[k], __popc(m));
+    }
+    base = __shfl_sync(FULLW, base, __ffs(m) - 1);
+    if (in) {
+        const int pos = base + __popc(m & ((1u << lane) - 1u));
+        if (pos < cap)
+            qlist[pos] = make_int2(k, q);
+        else
+            dev_fail(st, DEV_OVERFLOW, 58, node);
+    }
+}
+
+// every node above sub_n drew exactly sub_n members (keys are distinct)
+__global__ void k_sub_check(LevelBufs L, NodeArrays nd, int sub_n, rs_dev_status *st)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.K) return;
+    const int node = L.list[k], n = nd.count[node];
+    if (n > sub_n && L.sub_cnt[k] != sub_n) dev_fail(st, DEV_INTERNAL, 59, node);
+}
+
+// number of members whose nearest-neighbour distance sets a node's linking
+// length: all of them, or the subset's size above it
+__device__ __forceinline__ int n_select(int n, int sub_n) { return (sub_n > 0 && n > sub_n) ? sub_n : n; }
+
+__global__ void k_lvl_initk(LevelBufs L, NodeArrays nd, double f, int sub_n)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.K) return;
+    const int n = n_select(nd.count[L.list[k]], sub_n);
     long long kk = (long long)ceil(f * (double)n);
     if (kk < 1) kk = 1;
     if (kk > n) kk = n;
@@ -1944,9 +2099,10 @@ __global__ void __launch_bounds__(TQ) k_lvl_hist(LevelBufs L, NodeArrays nd, con
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
     const int q = q0 + threadIdx.x;
     if (q < n) {
+        // a negative value marks a member outside the node's subset
         unsigned bits = __float_as_uint(dnn[first + q]), digit, mask;
         sel_digit(bits, pass, digit, mask);
-        if ((bits & mask) == (L.sel_prefix[k] & mask)) atomicAdd(&h[digit], 1u);
+        if (!(bits >> 31) && (bits & mask) == (L.sel_prefix[k] & mask)) atomicAdd(&h[digit], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 2048; i += TQ)
@@ -1982,6 +2138,7 @@ __global__ void __launch_bounds__(TQ) k_lvl_band(LevelBufs L, NodeArrays nd, con
     const float blo = (float)((double)t32 * (1.0 - 2.0 * RS_BAND));
     const float bhi = (float)((double)t32 * (1.0 + 2.0 * RS_BAND));
     const float d = dnn[first + q];
+    if (__float_as_uint(d) >> 31) return;  // outside the subset
     if (d < blo) {
         atomicAdd(&L.below[k], 1);
     } else if (d <= bhi) {
@@ -2064,11 +2221,11 @@ __global__ void __launch_bounds__(W_WARPS * 32) k_lvl_band_exact(LevelBufs L, No
     if (lane == 0) L.band_val[b] = best;
 }
 
-__global__ void k_lvl_l2(LevelBufs L, NodeArrays nd, double f, rs_dev_status *st)
+__global__ void k_lvl_l2(LevelBufs L, NodeArrays nd, double f, int sub_n, rs_dev_status *st)
 {
     const int k = blockIdx.x;
     const int node = L.list[k];
-    const int n = nd.count[node];
+    const int n = n_select(nd.count[node], sub_n);
     long long kk = (long long)ceil(f * (double)n);
     if (kk < 1) kk = 1;
     if (kk > n) kk = n;
@@ -2259,7 +2416,7 @@ size_t tree_bytes(int64_t M, int64_t cap)
 // ---------------------------------------------------------------------------
 static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, int32_t stride, int64_t n, double box,
                              const int32_t *perm, const int64_t *goff, int64_t G, double f, int32_t min_n,
-                             int64_t node_cap, rs_tree **out)
+                             int64_t sub_n, uint64_t sub_seed, int64_t node_cap, rs_tree **out)
 {
     int64_t h[2];
     RS_TRY(rs_read_i64(ctx, goff, 1, h, "rs_refine6d"));
@@ -2326,7 +2483,7 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         *mid_q = q + 16 + 4 * cap;
     // ctr: [0] big_a len, [1] big_b len, [2] small len, [3] small head, [4] band len,
     // [6..7] bracket fallback flag, [8] tiny len, [9] tiny head, [10] k-d ranges,
-    // [11] middle len, [12] middle head
+    // [11] middle len, [12] middle head, [13] subset query list length
     RS_CUDA(ctx, cudaMemsetAsync(ctr, 0, sizeof(int) * 16, ctx->stream));
 
     const int gb = (int)std::min<int64_t>(G, (int64_t)ctx->num_sms * 8);
@@ -2376,7 +2533,7 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         RS_LAUNCH(ctx, "rf_lvl_tiles", k_lvl_tiles, K, 256, 0, (int)K, (const int64_t *)tiles, tl, tl + T);
         // per-rank state
         size_t per = sizeof(MomAcc) + sizeof(Metric6) + 2 * sizeof(float4) + 2048 * sizeof(unsigned) +
-                     4 * sizeof(int) + sizeof(double) + 64;
+                     7 * sizeof(int) + sizeof(double) + 64;
         RS_WS(ctx, char, rk, WS_RF_ACC, (int64_t)(per * K + 4096));
         char *rp = rk;
         L.acc = carve<MomAcc>(rp, K);
@@ -2388,6 +2545,8 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         L.sel_krem = carve<int>(rp, K);
         L.below = carve<int>(rp, K);
         L.tie = carve<int>(rp, K);
+        L.sub_t = carve<unsigned>(rp, 2 * K);
+        L.sub_cnt = carve<int>(rp, K);
         RS_CUDA(ctx, cudaMemsetAsync(rk, 0, (size_t)(rp - rk), ctx->stream));
         RS_WS(ctx, char, bandbuf, WS_RF_BAND, (int64_t)(LM * 16 + 64));
         char *bp = bandbuf;
@@ -2414,7 +2573,8 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
             RS_TRY(rs_read_i64(ctx, tot + 3, 1, &maxn, "rs_refine6d"));
             RS_WS(ctx, int64_t, kw, WS_RF_MISC5, 2 * (K + 1) + 8);
             int64_t *kseg = kw, *ktot = kw + (K + 1);
-            RS_LAUNCH(ctx, "rf_full_prep", k_full_prep, ceil_div(K, 256), 256, 0, (const int *)cur, (int)K, nd, kseg);
+            RS_LAUNCH(ctx, "rf_full_prep", k_full_prep, ceil_div(K, 256), 256, 0, (const int *)cur, (int)K, nd, kseg,
+                      0);
             RS_CUDA(ctx, cudaMemsetAsync(kseg + K, 0, sizeof(int64_t), ctx->stream));
             RS_TRY(rs_scan_i64(ctx, kseg, K + 1, ktot));
             int64_t NS;
@@ -2479,10 +2639,35 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         RS_LAUNCH(ctx, "rf_bvh_leaves", k_bvh_leaves, T, TQ, 0, L, nd, (const int64_t *)bo, boxes, ms,
                   (const float4 *)wpos, (const float4 *)wvel);
         RS_LAUNCH(ctx, "rf_bvh_build", k_bvh_build, K, 256, 0, L, nd, (const int64_t *)bo, boxes);
+        // ---- random member subsets of the nodes above sub_n (Sec. 3.2) ----
+        int2 *sub_q = nullptr;
+        int *sub_len = ctr + 13;
+        int64_t QN = 0, qcap = 0;
+        if (sub_n > 0) {
+            qcap = std::min<int64_t>(LM, K * sub_n);
+            RS_WS(ctx, int2, sq, WS_RF_SUBQ, qcap + 1);
+            sub_q = sq;
+            RS_CUDA(ctx, cudaMemsetAsync(sub_len, 0, sizeof(int), ctx->stream));
+            RS_LAUNCH(ctx, "rf_sub_init", k_sub_init, ceil_div(K, 128), 128, 0, L, nd, (int)sub_n);
+            for (int stage = 0; stage < 2; stage++) {
+                for (int pass = 0; pass < 3; pass++) {
+                    RS_LAUNCH(ctx, "rf_sub_hist", k_sub_hist, T, TQ, 0, L, nd, (const int *)widx,
+                              (unsigned long long)sub_seed, (int)sub_n, stage, pass);
+                    RS_LAUNCH(ctx, "rf_lvl_pick", k_lvl_pick, K, 32, 0, L, pass);
+                }
+                RS_LAUNCH(ctx, "rf_sub_stage", k_sub_stage, ceil_div(K, 128), 128, 0, L, stage);
+            }
+            RS_LAUNCH(ctx, "rf_sub_mark", k_sub_mark, T, TQ, 0, L, nd, (const int *)widx,
+                      (unsigned long long)sub_seed, (int)sub_n, dnn, sub_q, sub_len, (int)qcap, ctx->d_status);
+            RS_LAUNCH(ctx, "rf_sub_check", k_sub_check, ceil_div(K, 128), 128, 0, L, nd, (int)sub_n, ctx->d_status);
+            RS_TRY(rs_read_i64(ctx, sub_len, 1, &QN, "rs_refine6d"));
+            QN = std::min<int64_t>(QN & 0xffffffffll, qcap);
+        }
         // ---- linking length: sampled bracket, bounded nearest neighbours, exact select ----
         RS_WS(ctx, int64_t, ch, WS_RF_MISC4, 2 * (K + 1) + 8);
         int64_t *nsm = ch, *stot = ch + (K + 1);
-        RS_LAUNCH(ctx, "rf_smp_prep", k_smp_prep, ceil_div(K, 256), 256, 0, (const int *)cur, (int)K, nd, nsm);
+        RS_LAUNCH(ctx, "rf_smp_prep", k_smp_prep, ceil_div(K, 256), 256, 0, (const int *)cur, (int)K, nd, nsm,
+                  (int)sub_n);
         RS_CUDA(ctx, cudaMemsetAsync(nsm + K, 0, sizeof(int64_t), ctx->stream));
         RS_TRY(rs_scan_i64(ctx, nsm, K + 1, stot));
         int64_t SS;
@@ -2506,7 +2691,8 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         // every member's nearest-neighbour distance, searched from the radius
         RS_WS(ctx, int64_t, fw, WS_RF_MISC5, 2 * (K + 1) + 8);
         int64_t *nw = fw, *wtot = fw + (K + 1);
-        RS_LAUNCH(ctx, "rf_full_prep", k_full_prep, ceil_div(K, 256), 256, 0, (const int *)cur, (int)K, nd, nw);
+        RS_LAUNCH(ctx, "rf_full_prep", k_full_prep, ceil_div(K, 256), 256, 0, (const int *)cur, (int)K, nd, nw,
+                  (int)sub_n);
         RS_CUDA(ctx, cudaMemsetAsync(nw + K, 0, sizeof(int64_t), ctx->stream));
         RS_TRY(rs_scan_i64(ctx, nw, K + 1, wtot));
         int64_t W;
@@ -2521,7 +2707,11 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
                   jf + W, jf + 2 * W);
         RS_LAUNCH(ctx, "rf_lvl_nn", k_bvh_nn, ceil_div(W, W_WARPS), W_WARPS * 32, 0, L, JF, nd, (const int64_t *)bo,
                   boxes, ms, (const float *)R2, (const float *)STOP, dnn, ctx->d_status);
-        RS_LAUNCH(ctx, "rf_lvl_initk", k_lvl_initk, ceil_div(K, 128), 128, 0, L, nd, f);
+        if (QN > 0)
+            RS_LAUNCH(ctx, "rf_sub_nn", k_bvh_nn_list, ceil_div(QN, W_WARPS), W_WARPS * 32, 0, L, nd,
+                      (const int64_t *)bo, boxes, ms, (const int2 *)sub_q, (const int *)sub_len, (int)qcap, dnn,
+                      ctx->d_status);
+        RS_LAUNCH(ctx, "rf_lvl_initk", k_lvl_initk, ceil_div(K, 128), 128, 0, L, nd, f, (int)sub_n);
         for (int pass = 0; pass < 3; pass++) {
             RS_LAUNCH(ctx, "rf_lvl_hist", k_lvl_hist, T, TQ, 0, L, nd, (const float *)dnn, pass);
             RS_LAUNCH(ctx, "rf_lvl_pick", k_lvl_pick, K, 32, 0, L, pass);
@@ -2535,7 +2725,7 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
             RS_LAUNCH(ctx, "rf_lvl_nn_full", k_bvh_nn, ceil_div(W, W_WARPS), W_WARPS * 32, 0, L, JF, nd,
                       (const int64_t *)bo, boxes, ms, (const float *)nullptr, (const float *)nullptr, dnn,
                       ctx->d_status);
-            RS_LAUNCH(ctx, "rf_lvl_initk", k_lvl_initk, ceil_div(K, 128), 128, 0, L, nd, f);
+            RS_LAUNCH(ctx, "rf_lvl_initk", k_lvl_initk, ceil_div(K, 128), 128, 0, L, nd, f, (int)sub_n);
             for (int pass = 0; pass < 3; pass++) {
                 RS_LAUNCH(ctx, "rf_lvl_hist", k_lvl_hist, T, TQ, 0, L, nd, (const float *)dnn, pass);
                 RS_LAUNCH(ctx, "rf_lvl_pick", k_lvl_pick, K, 32, 0, L, pass);
@@ -2548,7 +2738,7 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         const int nbv = (int)(NB & 0xffffffffll);
         RS_LAUNCH(ctx, "rf_lvl_band_exact", k_lvl_band_exact, ceil_div(nbv, W_WARPS), W_WARPS * 32, 0, L, nd,
                   (const int64_t *)bo, boxes, ms, (const float *)dnn, ctx->d_status);
-        RS_LAUNCH(ctx, "rf_lvl_l2", k_lvl_l2, K, 128, 0, L, nd, f, ctx->d_status);
+        RS_LAUNCH(ctx, "rf_lvl_l2", k_lvl_l2, K, 128, 0, L, nd, f, (int)sub_n, ctx->d_status);
         RS_LAUNCH(ctx, "rf_lvl_iota", k_lvl_iota, T, TQ, 0, L, nd, uf, csize, cmin);
         RS_LAUNCH(ctx, "rf_bvh_linkbox", k_bvh_linkbox, K, 256, 0, L, nd, (const int64_t *)bo, boxes,
                   (const float4 *)wpos, (const float4 *)wvel, (const float *)dnn, uf, ctx->d_status);
@@ -2675,9 +2865,10 @@ extern "C" void rs_tree_free(rs_tree *t)
     delete t;
 }
 
-extern "C" rs_status rs_refine6d(rs_ctx *ctx, const float *pos, const float *vel, int32_t stride, int64_t n,
-                                 double box, const int32_t *perm, const int64_t *group_offsets, int64_t n_groups,
-                                 double f, int32_t min_n, rs_tree **out)
+extern "C" rs_status rs_refine6d_sampled(rs_ctx *ctx, const float *pos, const float *vel, int32_t stride, int64_t n,
+                                         double box, const int32_t *perm, const int64_t *group_offsets,
+                                         int64_t n_groups, double f, int32_t min_n, int64_t subset_n,
+                                         uint64_t subset_seed, rs_tree **out)
 {
     if (!ctx) return RS_ERR_INVALID_ARG;
     if (!out) return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_refine6d: out is NULL");
@@ -2685,6 +2876,8 @@ extern "C" rs_status rs_refine6d(rs_ctx *ctx, const float *pos, const float *vel
     if (n < 0 || n_groups < 0 || (stride != 3 && stride != 4) || !(box > 0) || !(f > 0 && f < 1) || min_n < 2 ||
         !group_offsets || (n > 0 && (!pos || !vel)) || (n_groups > 0 && !perm))
         return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_refine6d: bad argument");
+    if (subset_n != 0 && (subset_n < SMALL_N || subset_n >= ((int64_t)1 << 31)))
+        return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_refine6d: subset size must be 0 or in [1024, 2^31)");
     if (n >= ((int64_t)1 << 31)) return rs_fail(ctx, RS_ERR_TOO_LARGE, "rs_refine6d: n >= 2^31");
     if ((double)(float)box != box) return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_refine6d: box must be a float32 value");
     int64_t cap = 0;
@@ -2699,7 +2892,8 @@ extern "C" rs_status rs_refine6d(rs_ctx *ctx, const float *pos, const float *vel
     }
     for (int attempt = 0; attempt < 4; attempt++) {
         rs_tree *t = nullptr;
-        rs_status s = refine_impl(ctx, pos, vel, stride, n, box, perm, group_offsets, n_groups, f, min_n, cap, &t);
+        rs_status s = refine_impl(ctx, pos, vel, stride, n, box, perm, group_offsets, n_groups, f, min_n, subset_n,
+                                  subset_seed, cap, &t);
         if (s == RS_OK) {
             *out = t;
             return RS_OK;
@@ -2716,6 +2910,13 @@ extern "C" rs_status rs_refine6d(rs_ctx *ctx, const float *pos, const float *vel
         cap *= 4;
     }
     return rs_fail(ctx, RS_ERR_INTERNAL, "rs_refine6d: node capacity");
+}
+
+extern "C" rs_status rs_refine6d(rs_ctx *ctx, const float *pos, const float *vel, int32_t stride, int64_t n,
+                                 double box, const int32_t *perm, const int64_t *group_offsets, int64_t n_groups,
+                                 double f, int32_t min_n, rs_tree **out)
+{
+    return rs_refine6d_sampled(ctx, pos, vel, stride, n, box, perm, group_offsets, n_groups, f, min_n, 0, 0, out);
 }
 
 extern "C" rs_status rs_tree_info(const rs_tree *t, int64_t *n_nodes, int32_t *n_levels, int64_t *n_seeds,

@@ -31,7 +31,8 @@ class RsError(RuntimeError):
 
 class rs_params(C.Structure):
     _fields_ = [("b", C.c_double), ("f", C.c_double), ("min_n", C.c_int32), ("delta_vir", C.c_double),
-                ("nbar", C.c_double), ("merge_thresh", C.c_double)]
+                ("nbar", C.c_double), ("merge_thresh", C.c_double), ("nn_subset", C.c_int64),
+                ("nn_seed", C.c_uint64)]
 
 
 class rs_stats(C.Structure):
@@ -57,6 +58,8 @@ def _declare(lib):
         "rs_fof3d": (C.c_int, [P, P, i32, i64, f64, f64, P, P, P]),
         "rs_group_sort": (C.c_int, [P, P, i64, i32, P, P, i64, C.POINTER(i64), C.POINTER(i64)]),
         "rs_refine6d": (C.c_int, [P, P, P, i32, i64, f64, P, P, i64, f64, i32, C.POINTER(P)]),
+        "rs_refine6d_sampled": (C.c_int, [P, P, P, i32, i64, f64, P, P, i64, f64, i32, i64, C.c_uint64,
+                                          C.POINTER(P)]),
         "rs_tree_info": (C.c_int, [P, C.POINTER(i64), C.POINTER(i32), C.POINTER(i64), C.POINTER(i64),
                                    C.POINTER(i64)]),
         "rs_tree_nodes": (C.c_int, [P, P] + [P] * 12),
@@ -246,13 +249,22 @@ class Tree:
 def rs_refine6d(ctx: Context, pos: torch.Tensor, vel: torch.Tensor, box: float, perm: torch.Tensor,
                 offsets: torch.Tensor, f: float = 0.7, min_n: int = 10) -> Tree:
     """Sec. 3.2."""
+    return rs_refine6d_sampled(ctx, pos, vel, box, perm, offsets, f, min_n, 0, 0)
+
+
+def rs_refine6d_sampled(ctx: Context, pos: torch.Tensor, vel: torch.Tensor, box: float, perm: torch.Tensor,
+                        offsets: torch.Tensor, f: float = 0.7, min_n: int = 10, subset_n: int = 10000,
+                        subset_seed: int = 0) -> Tree:
+    """Sec. 3.2 with the linking length of nodes above subset_n members taken
+    from a random subset_n-member subset (subset_n = 0: every member)."""
     stride = _stride_of(pos)
     if _stride_of(vel) != stride:
         raise ValueError("pos and vel must have the same stride")
     h = C.c_void_p()
     ng = offsets.shape[0] - 1
-    ctx.check(lib().rs_refine6d(ctx.handle, _ptr(pos), _ptr(vel), stride, pos.shape[0], float(box), _ptr(perm),
-                                C.c_void_p(offsets.data_ptr()), ng, float(f), int(min_n), C.byref(h)))
+    ctx.check(lib().rs_refine6d_sampled(ctx.handle, _ptr(pos), _ptr(vel), stride, pos.shape[0], float(box),
+                                        _ptr(perm), C.c_void_p(offsets.data_ptr()), ng, float(f), int(min_n),
+                                        int(subset_n), int(subset_seed) & (2 ** 64 - 1), C.byref(h)))
     return Tree(ctx, h, pos.shape[0], pos.device)
 
 

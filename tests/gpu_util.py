@@ -90,11 +90,14 @@ def compare_trees(g, o, box, rel=1e-6):
     return matched, len(diff)
 
 
-def run_gpu_path(ctx, rs, cat, stride=3, f=0.7, min_n=10, b=0.28, assign=True):
+def run_gpu_path(ctx, rs, cat, stride=3, f=0.7, min_n=10, b=0.28, assign=True, sub_n=0, sub_seed=0):
     pos, vel = cuda_inputs(cat, stride)
     labels, ng, nt = rs.rs_fof3d(ctx, pos, cat.box, b, want_groups=True, want_tieband=True)
     perm, offsets = rs.rs_group_sort(ctx, labels, min_n)
-    tree = rs.rs_refine6d(ctx, pos, vel, cat.box, perm, offsets, f, min_n)
+    if sub_n:
+        tree = rs.rs_refine6d_sampled(ctx, pos, vel, cat.box, perm, offsets, f, min_n, sub_n, sub_seed)
+    else:
+        tree = rs.rs_refine6d(ctx, pos, vel, cat.box, perm, offsets, f, min_n)
     out = dict(labels=labels.cpu().numpy(), n_groups=ng, tie3=nt, perm=perm.cpu().numpy(),
                offsets=offsets.cpu().numpy(), tree=tree)
     if assign:
@@ -103,5 +106,6 @@ def run_gpu_path(ctx, rs, cat, stride=3, f=0.7, min_n=10, b=0.28, assign=True):
     return out
 
 
-def run_oracle_path(cat, f=0.7, min_n=10, b=0.28, assign=True):
-    return oracle.run_all(cat.pos, cat.vel, cat.box, b=b, f=f, min_n=min_n, assign_too=assign)
+def run_oracle_path(cat, f=0.7, min_n=10, b=0.28, assign=True, sub_n=0, sub_seed=0):
+    return oracle.run_all(cat.pos, cat.vel, cat.box, b=b, f=f, min_n=min_n, assign_too=assign, sub_n=sub_n,
+                          sub_seed=sub_seed)

@@ -118,9 +118,9 @@ def test_group_sort_c1(rs, ctx):
 # ---------------------------------------------------------------------------
 # hierarchy and assignment
 # ---------------------------------------------------------------------------
-def _check_all(rs, ctx, cat, stride=3, f=0.7, min_n=10):
-    g = run_gpu_path(ctx, rs, cat, stride=stride, f=f, min_n=min_n)
-    o = run_oracle_path(cat, f=f, min_n=min_n)
+def _check_all(rs, ctx, cat, stride=3, f=0.7, min_n=10, sub_n=0, sub_seed=0):
+    g = run_gpu_path(ctx, rs, cat, stride=stride, f=f, min_n=min_n, sub_n=sub_n, sub_seed=sub_seed)
+    o = run_oracle_path(cat, f=f, min_n=min_n, sub_n=sub_n, sub_seed=sub_seed)
     assert np.array_equal(g["labels"], o["labels"])
     assert np.array_equal(g["perm"], o["members"]) and np.array_equal(g["offsets"], o["offsets"])
     gd, od = gpu_tree_dict(g["tree"]), oracle_tree_dict(o["tree"])
@@ -150,9 +150,7 @@ def test_refine_stride4_and_f_values(rs, ctx):
     _check_all(rs, ctx, c, f=0.9, min_n=20)
 
 
-def test_refine_big_node_path(rs, ctx):
-    """Groups above 1024 members take the multi-CTA level path; their
-    children below it finish in the one-CTA subtree kernel."""
+def _big_catalogue():
     rng = np.random.default_rng(3)
     box = 20.0
     parts, vels = [], []
@@ -170,10 +168,48 @@ def test_refine_big_node_path(rs, ctx):
     vel = np.vstack(vels).astype(np.float32)
     n = len(pos)
     perm = rng.permutation(n)
-    c = synth.Catalogue(pos=pos[perm].copy(), vel=vel[perm].copy(), box=box, truth=np.zeros(n, np.int32),
-                        comp_parent=np.zeros(0, np.int32), comp_n=np.zeros(0))
-    matched, excused, info = _check_all(rs, ctx, c)
+    return synth.Catalogue(pos=pos[perm].copy(), vel=vel[perm].copy(), box=box, truth=np.zeros(n, np.int32),
+                           comp_parent=np.zeros(0, np.int32), comp_n=np.zeros(0))
+
+
+def test_refine_big_node_path(rs, ctx):
+    """Groups above 1024 members take the multi-CTA level path; their
+    children below it finish in the one-CTA subtree kernel."""
+    matched, excused, info = _check_all(rs, ctx, _big_catalogue())
     assert info.n_levels >= 3
+
+
+@pytest.mark.parametrize("sub_n,seed", [(1024, 0), (2048, 7), (4096, 2 ** 63 + 5)])
+def test_refine_sampled_subsets(rs, ctx, sub_n, seed):
+    """Sec. 3.2 subset linking lengths: nodes above sub_n members take l from
+    the nearest-neighbour distances of their sub_n smallest-key members."""
+    c = _big_catalogue()
+    matched, excused, info = _check_all(rs, ctx, c, sub_n=sub_n, sub_seed=seed)
+    sizes = np.bincount(oracle.fof3d(c.pos, c.box)[0])
+    assert sizes.max() > sub_n  # at least the largest root is sampled
+    assert matched >= 5
+
+
+def test_refine_sampled_covering_subset_is_exact(rs, ctx):
+    """A subset at least as large as every node is the exact linking length:
+    the same tree bit for bit."""
+    c = _big_catalogue()
+    a = run_gpu_path(ctx, rs, c, assign=False)
+    b = run_gpu_path(ctx, rs, c, assign=False, sub_n=len(c.pos), sub_seed=9)
+    da, db = gpu_tree_dict(a["tree"]), gpu_tree_dict(b["tree"])
+    assert da.keys() == db.keys()
+    for k in da:
+        assert da[k]["members"] == db[k]["members"] and da[k]["lnk"] == db[k]["lnk"]
+
+
+def test_refine_sampled_bad_subset_size(rs, ctx):
+    c = _small(11)
+    pos, vel = cuda_inputs(c)
+    labels, _, _ = rs.rs_fof3d(ctx, pos, c.box, 0.28)
+    perm, offsets = rs.rs_group_sort(ctx, labels, 10)
+    for bad in (1, 1023, -5):
+        with pytest.raises(RuntimeError):
+            rs.rs_refine6d_sampled(ctx, pos, vel, c.box, perm, offsets, 0.7, 10, bad, 0)
 
 
 def test_refine_group_across_box_corner(rs, ctx):
@@ -249,3 +285,11 @@ def test_deterministic_repeat(rs, ctx):
 def test_full_path_c2(rs, ctx):
     matched, excused, info = _check_all(rs, ctx, synth.generate("c2"))
     print(f"c2: nodes {info.n_nodes} matched {matched} excused {excused} tie {info.n_tieband}")
+
+
+@pytest.mark.slow
+def test_full_path_c2_subset_10000(rs, ctx):
+    """The paper's setting: groups above 10,000 particles take their linking
+    length from a random 10,000-particle subset (Sec. 3.2)."""
+    matched, excused, info = _check_all(rs, ctx, synth.generate("c2"), sub_n=10000, sub_seed=11104372)
+    print(f"c2 subset: nodes {info.n_nodes} matched {matched} excused {excused} tie {info.n_tieband}")
