@@ -48,6 +48,8 @@ def _load():
     i64, i32, f64 = C.c_int64, C.c_int32, C.c_double
     lib.or_version.restype = i64
     lib.or_fof3d.argtypes = [P, i64, f64, f64, P, P]
+    lib.or_fof3d_accel.argtypes = [P, i64, f64, f64, i64, P, P]
+    lib.or_fof3d_accel.restype = C.c_int
     lib.or_fof3d.restype = C.c_int
     lib.or_fof3d_tieband.argtypes = [P, i64, f64, f64]
     lib.or_fof3d_tieband.restype = i64
@@ -117,6 +119,24 @@ def fof3d(pos, box: float, b: float = 0.28, l: float | None = None):
     if st:
         raise RuntimeError(f"or_fof3d failed with status {st}")
     return labels, l, int(tie.value)
+
+
+def fof3d_accel(pos, box: float, b: float = 0.28, l: float | None = None, dense_n: int = 16):
+    """Sec. 3.1, the accelerated variant: particles in index order; one with
+    more than dense_n neighbours within l joins everything within 2l and its
+    neighbours skip their own search.  Returns (labels, l, n_centres), labels
+    being the smallest particle index of each group and n_centres the number
+    of particles that searched 2l."""
+    pos = _f32(pos)
+    n = pos.shape[0]
+    if l is None:
+        l = linking_length(n, box, b) if n > 0 else 0.0
+    labels = np.empty(n, np.int32)
+    nc = C.c_int64(0)
+    st = _load().or_fof3d_accel(_ptr(pos), n, float(box), float(l), int(dense_n), _ptr(labels), C.byref(nc))
+    if st:
+        raise RuntimeError(f"or_fof3d_accel failed with status {st}")
+    return labels, l, int(nc.value)
 
 
 def fof3d_tieband(pos, box: float, l: float) -> int:
