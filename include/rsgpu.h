@@ -5,6 +5,7 @@
  * the ROCKSTAR halo finder does (Behroozi, Wechsler & Wu, arXiv:1110.4372):
  *
  *   rs_fof3d       3D friends-of-friends over the box                Sec. 3.1
+ *   rs_fof3d_accel the paper's accelerated variant of it             Sec. 3.1
  *   rs_group_sort  groups of at least min_n particles as a CSR list  Sec. 3.1, App. A
  *   rs_refine6d    phase-space FOF hierarchy inside every group      Sec. 3.2, Eq. 1
  *   rs_refine6d_sampled  the same with subset linking lengths        Sec. 3.2
@@ -99,11 +100,28 @@ double rs_linking_length(int64_t n, double box, double b);
  *   n_tieband (host, optional) number of pairs with |d - l| <= 1e-6 l; asking
  *             for it runs an extra pass over every pair within 2 l.
  * Passing either host pointer synchronises.  Errors: RS_ERR_INVALID_ARG for
- * box <= 0, b <= 0, stride not 3 or 4, or a box narrower than about seven
- * linking lengths; RS_ERR_TOO_LARGE for n >= 2^31 or more than 2^32 grid
- * cells of side 4 l / sqrt 3. */
+ * box <= 0, b <= 0, stride not 3 or 4, a box narrower than about seven
+ * linking lengths, or a box below 14 linking lengths for which no grid of
+ * 4k cells per side has cells between l/2 and l/sqrt 3 (box/l in 4.6-6.4,
+ * 6.9-8.1, 9.2-10.1, 11.5-12.1 or 13.9-14.1, roughly); RS_ERR_TOO_LARGE for
+ * n >= 2^31 or more than 2^32 grid cells of side 4 l / sqrt 3. */
 rs_status rs_fof3d(rs_ctx *ctx, const float *pos, int32_t stride, int64_t n, double box, double b,
                    int32_t *labels, int64_t *n_groups, int64_t *n_tieband);
+
+/* The paper's accelerated 3D FOF (Sec. 3.1): a particle with more than
+ * dense_n other particles within l (the paper's 16) is joined with every
+ * particle within 2l, and the neighbour search of its neighbours within l is
+ * skipped.  Particles are taken in index order, which gives the closed form
+ * computed here: a dense particle is a "centre" when no centre of smaller
+ * index lies within l; groups are the components of the plain FOF graph
+ * plus an edge from every centre to every particle within 2l (inclusive).
+ * Every group is a union of plain FOF groups.  labels as rs_fof3d (device,
+ * n int32).  n_groups and n_centres (host, optional; n_centres = number of
+ * centres) synchronise.  The call always synchronises once per round of the
+ * centre choice.  Errors as rs_fof3d; RS_ERR_INVALID_ARG for dense_n < 0;
+ * RS_ERR_INTERNAL if the centre choice has not settled after 65536 rounds. */
+rs_status rs_fof3d_accel(rs_ctx *ctx, const float *pos, int32_t stride, int64_t n, double box, double b,
+                         int32_t dense_n, int32_t *labels, int64_t *n_groups, int64_t *n_centres);
 
 /* Groups with at least min_n members as a CSR list -- the work units of
  * App. A.  perm (device, capacity n) receives the members of each such group

@@ -19,6 +19,7 @@
 // separate multiplies and adds as the definition, so the partition is the
 // float64 one.
 #include <cmath>
+#include <utility>
 
 #include "rs_internal.cuh"
 
@@ -416,6 +417,168 @@ __global__ void __launch_bounds__(FOF_THREADS) k_fof_tieband(const uint32_t *n_c
     if (lane_id() == 0 && c) atomicAdd(count, c);
 }
 
+// ---- accelerated variant (Sec. 3.1) ----
+// The paper's faster FOF visits particles one by one: a particle with more
+// than dense_n neighbours within l joins every particle within 2l, and its
+// neighbours skip their own search.  Taking the visit order to be the
+// particle index, the groups have a closed form that needs no order: call a
+// dense particle a centre when no centre of smaller index lies within l (the
+// index-greedy maximal independent set of the dense particles); the groups
+// are the components of the plain FOF graph plus an edge from every centre
+// to every particle within 2l of it (a skipped particle lies within l of a
+// centre, so its own FOF edges end within 2l of that centre).  So the plain
+// FOF runs first, then: neighbour counts up to dense_n + 1; rounds that
+// decide the centres (a dense particle becomes a centre once every dense
+// neighbour of smaller index is decided and none is a centre, and drops out
+// once one is a centre); and the 2l joins of the centres' fine cells.
+enum : uint8_t { ACC_SPARSE = 0, ACC_UNDECIDED = 1, ACC_CENTRE = 2, ACC_OUT = 3 };
+
+// Calls f(B, b0, b1, sx, sy, sz) for every occupied fine cell B within R fine
+// cells per axis of the fine cell at fine coordinates (ax, ay, az) (coarse
+// cell (ccx, ccy, ccz), sub-cell (ux, uy, uz)), with B's particle range and
+// the periodic shifts; stops when f returns true.  Visits the 27 coarse
+// cells around the query's, which hold every fine cell within R <= 4.
+template <typename F>
+__device__ __forceinline__ void acc_cells(int ccx, int ccy, int ccz, int ux, int uy, int uz, int R,
+                                          const uint32_t *cell_start, const uint32_t *table, const uint64_t *occ,
+                                          const FofGeom &g, F f)
+{
+    const int ax = 4 * ccx + ux, ay = 4 * ccy + uy, az = 4 * ccz + uz;
+    for (int dz = -1; dz <= 1; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                uint64_t cand = reach_mask(ux, uy, uz, dx, dy, dz, R);
+                if (!cand) continue;
+                int cx = ccx + dx, cy = ccy + dy, cz = ccz + dz;
+                cx = cx < 0 ? cx + g.Gc : (cx >= g.Gc ? cx - g.Gc : cx);
+                cy = cy < 0 ? cy + g.Gc : (cy >= g.Gc ? cy - g.Gc : cy);
+                cz = cz < 0 ? cz + g.Gc : (cz >= g.Gc ? cz - g.Gc : cz);
+                const uint64_t cc = ((uint64_t)cz * g.Gc + cy) * g.Gc + cx;
+                const uint32_t b0c = table[cc];
+                if (b0c == 0xffffffffu) continue;
+                const uint64_t om = occ[b0c];
+                cand &= om;
+                while (cand) {
+                    const int sb = __ffsll((long long)cand) - 1;
+                    cand &= cand - 1ull;
+                    const uint32_t B = b0c + (uint32_t)__popcll(om & ((1ull << sb) - 1ull));
+                    const int bx = 4 * cx + (sb & 3), by = 4 * cy + ((sb >> 2) & 3), bz = 4 * cz + (sb >> 4);
+                    int sx, sy, sz;
+                    fine_offset(ax, bx, g.Gf, sx);
+                    fine_offset(ay, by, g.Gf, sy);
+                    fine_offset(az, bz, g.Gf, sz);
+                    if (f(B, cell_start[B], cell_start[B + 1], sx, sy, sz)) return;
+                }
+            }
+}
+
+__device__ __forceinline__ void acc_where(const uint64_t *cell_key, uint32_t A, const FofGeom &g, int &ccx, int &ccy,
+                                          int &ccz, int &ux, int &uy, int &uz)
+{
+    const uint64_t k = cell_key[A];
+    const int sa = (int)(k & 63);
+    ux = sa & 3;
+    uy = (sa >> 2) & 3;
+    uz = sa >> 4;
+    coarse_coords(k >> 6, g.Gc, ccx, ccy, ccz);
+}
+
+// dense flag of every particle (sorted slot q): more than dense_n others
+// within l.  The own fine cell is a clique; other cells are tested pair by
+// pair until the count is exceeded.
+__global__ void __launch_bounds__(FOF_THREADS) k_acc_count(int64_t n, const uint32_t *cell_of, const uint64_t *cell_key,
+                                                           const uint32_t *cell_start, const uint32_t *table,
+                                                           const uint64_t *occ, const float4 *spos, FofGeom g,
+                                                           int dense_n, uint8_t *state)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const uint32_t A = cell_of[q];
+    int cnt = (int)(cell_start[A + 1] - cell_start[A]) - 1;
+    if (cnt <= dense_n) {
+        int ccx, ccy, ccz, ux, uy, uz;
+        acc_where(cell_key, A, g, ccx, ccy, ccz, ux, uy, uz);
+        const float4 p = spos[q];
+        acc_cells(ccx, ccy, ccz, ux, uy, uz, 2, cell_start, table, occ, g,
+                  [&](uint32_t B, uint32_t b0, uint32_t b1, int sx, int sy, int sz) {
+                      if (B == A) return false;
+                      for (uint32_t r = b0; r < b1; r++)
+                          if (pair_link(p, spos[r], sx, sy, sz, g) && ++cnt > dense_n) return true;
+                      return false;
+                  });
+    }
+    state[q] = cnt > dense_n ? ACC_UNDECIDED : ACC_SPARSE;
+}
+
+// one round of the centre choice; `left` counts the particles still undecided
+__global__ void __launch_bounds__(FOF_THREADS) k_acc_round(int64_t n, const uint32_t *cell_of, const uint64_t *cell_key,
+                                                           const uint32_t *cell_start, const uint32_t *table,
+                                                           const uint64_t *occ, const float4 *spos, const uint32_t *idx,
+                                                           FofGeom g, const uint8_t *sin, uint8_t *sout,
+                                                           unsigned long long *left)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const uint8_t s0 = sin[q];
+    if (s0 != ACC_UNDECIDED) {
+        sout[q] = s0;
+        return;
+    }
+    const uint32_t A = cell_of[q], me = idx[q];
+    int ccx, ccy, ccz, ux, uy, uz;
+    acc_where(cell_key, A, g, ccx, ccy, ccz, ux, uy, uz);
+    const float4 p = spos[q];
+    bool blocked = false, out = false;
+    acc_cells(ccx, ccy, ccz, ux, uy, uz, 2, cell_start, table, occ, g,
+              [&](uint32_t B, uint32_t b0, uint32_t b1, int sx, int sy, int sz) {
+                  for (uint32_t r = b0; r < b1; r++) {
+                      const uint8_t sr = sin[r];
+                      if ((sr != ACC_UNDECIDED && sr != ACC_CENTRE) || idx[r] >= me) continue;
+                      // the own fine cell is a clique
+                      if (B != A && !pair_link(p, spos[r], sx, sy, sz, g)) continue;
+                      if (sr == ACC_CENTRE) {
+                          out = true;
+                          return true;
+                      }
+                      blocked = true;
+                  }
+                  return false;
+              });
+    const uint8_t s1 = out ? ACC_OUT : (blocked ? ACC_UNDECIDED : ACC_CENTRE);
+    sout[q] = s1;
+    if (s1 == ACC_UNDECIDED) atomicAdd(left, 1ull);
+}
+
+// every centre joins the fine cells that hold a particle within 2l of it
+// (a fine cell is one set already, so one such particle joins it); g2 is the
+// geometry with the thresholds of 2l
+__global__ void __launch_bounds__(FOF_THREADS) k_acc_join(int64_t n, const uint32_t *cell_of, const uint64_t *cell_key,
+                                                          const uint32_t *cell_start, const uint32_t *table,
+                                                          const uint64_t *occ, const float4 *spos, FofGeom g2,
+                                                          const uint8_t *state, int *parent,
+                                                          unsigned long long *centres, rs_dev_status *st)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool mine = q < n && state[q] == ACC_CENTRE;
+    const unsigned m = __ballot_sync(0xffffffffu, mine);
+    if (lane_id() == 0 && m) atomicAdd(centres, (unsigned long long)__popc(m));
+    if (!mine) return;
+    const uint32_t A = cell_of[q];
+    int ccx, ccy, ccz, ux, uy, uz;
+    acc_where(cell_key, A, g2, ccx, ccy, ccz, ux, uy, uz);
+    const float4 p = spos[q];
+    acc_cells(ccx, ccy, ccz, ux, uy, uz, 4, cell_start, table, occ, g2,
+              [&](uint32_t B, uint32_t b0, uint32_t b1, int sx, int sy, int sz) {
+                  if (uf_find(parent, (int)A, st) == uf_find(parent, (int)B, st)) return false;
+                  for (uint32_t r = b0; r < b1; r++)
+                      if (pair_link(p, spos[r], sx, sy, sz, g2)) {
+                          uf_union(parent, (int)A, (int)B, st);
+                          break;
+                      }
+                  return false;
+              });
+}
+
 rs_status fof_geometry(rs_ctx *ctx, int64_t n, double box, double b, FofGeom *g)
 {
     double l = rs_linking_length(n, box, b);
@@ -432,6 +595,14 @@ rs_status fof_geometry(rs_ctx *ctx, int64_t n, double box, double b, FofGeom *g)
     g->Gc = (int32_t)gc;
     g->Gf = 4 * g->Gc;
     if (g->Gf > gf_est) return rs_fail(ctx, RS_ERR_INTERNAL, "rs_fof3d: grid estimate");
+    // the link kernels look two fine cells per axis around a cell: two
+    // friends' fine indices differ by less than 1 + l/s + 2 err, so l/s must
+    // not exceed 2 - 2 err.  With s rounded down to box / (4 Gc) this fails
+    // only in narrow windows of box/l below 14 (e.g. 6.9-8, 11.55-12).
+    if (l * (double)g->Gf / box > 2.0 - 2.0 * err)
+        return rs_fail(ctx, RS_ERR_INVALID_ARG,
+                       "rs_fof3d: no cell grid fits this box and linking length (cells of side between l/2 and "
+                       "l/sqrt(3) that divide the box 4k times); use a box of at least 14 linking lengths");
     g->inv_sf = (float)((double)g->Gf / box);
     g->boxf = (float)box;
     g->box = box;
@@ -453,8 +624,13 @@ int key_bits(const FofGeom &g)
 
 }  // namespace
 
-extern "C" rs_status rs_fof3d(rs_ctx *ctx, const float *pos, int32_t stride, int64_t n, double box, double b,
-                              int32_t *labels, int64_t *n_groups, int64_t *n_tieband)
+namespace {
+
+constexpr int ACC_MAX_ROUNDS = 1 << 16;  // bound on the centre-choice rounds
+
+// plain FOF (dense_n < 0) or the accelerated variant (dense_n >= 0)
+rs_status fof_run(rs_ctx *ctx, const float *pos, int32_t stride, int64_t n, double box, double b, int32_t dense_n,
+                  int32_t *labels, int64_t *n_groups, int64_t *n_tieband, int64_t *n_centres)
 {
     if (!ctx) return RS_ERR_INVALID_ARG;
     if (n < 0 || (n > 0 && (!pos || !labels)) || (stride != 3 && stride != 4) || !(box > 0) || !(b > 0))
@@ -463,6 +639,7 @@ extern "C" rs_status rs_fof3d(rs_ctx *ctx, const float *pos, int32_t stride, int
     if (n == 0) {
         if (n_groups) *n_groups = 0;
         if (n_tieband) *n_tieband = 0;
+        if (n_centres) *n_centres = 0;
         return RS_OK;
     }
     FofGeom g;
@@ -513,6 +690,39 @@ extern "C" rs_status rs_fof3d(rs_ctx *ctx, const float *pos, int32_t stride, int
         RS_LAUNCH(ctx, "fof_link", k_fof_link, grid, T, 0, (const uint32_t *)n_cells, (const uint64_t *)cell_key,
                   (const uint32_t *)cell_start, (const uint32_t *)table, (const uint64_t *)occ, (const float4 *)spos,
                   parent, g, pass, ctx->d_status);
+    if (dense_n >= 0) {
+        // accelerated variant: dense flags, centre rounds, 2l joins
+        RS_WS(ctx, uint8_t, acc, WS_FOF_ACC, 2 * n + 64);
+        uint8_t *sa = acc, *sb = acc + n;
+        unsigned long long *acnt = (unsigned long long *)(acc + (2 * n + 7) / 8 * 8);
+        RS_LAUNCH(ctx, "fof_acc_count", k_acc_count, nb, T, 0, n, (const uint32_t *)cell_of,
+                  (const uint64_t *)cell_key, (const uint32_t *)cell_start, (const uint32_t *)table,
+                  (const uint64_t *)occ, (const float4 *)spos, g, (int)dense_n, sa);
+        for (int round = 0;; round++) {
+            if (round >= ACC_MAX_ROUNDS)
+                return rs_fail(ctx, RS_ERR_INTERNAL, "rs_fof3d_accel: the centre choice did not settle");
+            RS_CUDA(ctx, cudaMemsetAsync(acnt, 0, sizeof(unsigned long long), ctx->stream));
+            RS_LAUNCH(ctx, "fof_acc_round", k_acc_round, nb, T, 0, n, (const uint32_t *)cell_of,
+                      (const uint64_t *)cell_key, (const uint32_t *)cell_start, (const uint32_t *)table,
+                      (const uint64_t *)occ, (const float4 *)spos, (const uint32_t *)idx, g, (const uint8_t *)sa, sb,
+                      acnt);
+            int64_t left = 0;
+            RS_TRY(rs_read_i64(ctx, acnt, 1, &left, "rs_fof3d_accel"));
+            std::swap(sa, sb);
+            if (left == 0) break;
+        }
+        // the same tests at 2l: every threshold scales by exactly 2 or 4
+        FofGeom g2 = g;
+        g2.l = 2.0 * g.l;
+        g2.l2 = 4.0 * g.l2;
+        g2.lo32 = 4.0f * g.lo32;
+        g2.hi32 = 4.0f * g.hi32;
+        RS_CUDA(ctx, cudaMemsetAsync(acnt + 1, 0, sizeof(unsigned long long), ctx->stream));
+        RS_LAUNCH(ctx, "fof_acc_join", k_acc_join, nb, T, 0, n, (const uint32_t *)cell_of, (const uint64_t *)cell_key,
+                  (const uint32_t *)cell_start, (const uint32_t *)table, (const uint64_t *)occ, (const float4 *)spos,
+                  g2, (const uint8_t *)sa, parent, acnt + 1, ctx->d_status);
+        if (n_centres) RS_TRY(rs_read_i64(ctx, acnt + 1, 1, n_centres, "rs_fof3d_accel"));
+    }
     RS_LAUNCH(ctx, "fof_rootmin", k_fof_rootmin, grid, T, 0, (const uint32_t *)n_cells,
               (const uint32_t *)cell_start, (const uint32_t *)idx, parent, root_min, ctx->d_status);
     RS_LAUNCH(ctx, "fof_labels", k_fof_labels, nb, T, 0, n, (const uint32_t *)idx, (const uint32_t *)cell_of,
@@ -533,6 +743,21 @@ extern "C" rs_status rs_fof3d(rs_ctx *ctx, const float *pos, int32_t stride, int
         if (n_tieband) *n_tieband = h[1];
     }
     return RS_OK;
+}
+
+}  // namespace
+
+extern "C" rs_status rs_fof3d(rs_ctx *ctx, const float *pos, int32_t stride, int64_t n, double box, double b,
+                              int32_t *labels, int64_t *n_groups, int64_t *n_tieband)
+{
+    return fof_run(ctx, pos, stride, n, box, b, -1, labels, n_groups, n_tieband, nullptr);
+}
+
+extern "C" rs_status rs_fof3d_accel(rs_ctx *ctx, const float *pos, int32_t stride, int64_t n, double box, double b,
+                                    int32_t dense_n, int32_t *labels, int64_t *n_groups, int64_t *n_centres)
+{
+    if (ctx && dense_n < 0) return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_fof3d_accel: dense_n must be >= 0");
+    return fof_run(ctx, pos, stride, n, box, b, dense_n, labels, n_groups, nullptr, n_centres);
 }
 
 // ---------------------------------------------------------------------------

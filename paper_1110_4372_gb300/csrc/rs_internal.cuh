@@ -48,7 +48,7 @@ enum rs_ws_slot {
     WS_SCAN_TMP = 0,
     WS_SORT_K0, WS_SORT_K1, WS_SORT_V0, WS_SORT_V1, WS_SORT_HIST,
     WS_FOF_CELLKEY, WS_FOF_CELLSTART, WS_FOF_CELLOF, WS_FOF_PARENT, WS_FOF_ROOTMIN, WS_FOF_TABLE,
-    WS_FOF_OCC, WS_FOF_POS4, WS_FOF_MISC,
+    WS_FOF_OCC, WS_FOF_POS4, WS_FOF_MISC, WS_FOF_ACC,
     WS_GS_COUNT, WS_GS_FLAG,
     WS_RF_POS, WS_RF_VEL, WS_RF_POS2, WS_RF_VEL2, WS_RF_IDX2,
     WS_RF_DNN, WS_RF_PARENT, WS_RF_MISC0, WS_RF_MISC1, WS_RF_MISC2, WS_RF_MISC3, WS_RF_NODEQ,

@@ -56,6 +56,7 @@ def _declare(lib):
         "rs_last_error": (C.c_char_p, [P]),
         "rs_linking_length": (f64, [i64, f64, f64]),
         "rs_fof3d": (C.c_int, [P, P, i32, i64, f64, f64, P, P, P]),
+        "rs_fof3d_accel": (C.c_int, [P, P, i32, i64, f64, f64, i32, P, P, P]),
         "rs_group_sort": (C.c_int, [P, P, i64, i32, P, P, i64, C.POINTER(i64), C.POINTER(i64)]),
         "rs_refine6d": (C.c_int, [P, P, P, i32, i64, f64, P, P, i64, f64, i32, C.POINTER(P)]),
         "rs_refine6d_sampled": (C.c_int, [P, P, P, i32, i64, f64, P, P, i64, f64, i32, i64, C.c_uint64,
@@ -165,6 +166,19 @@ def rs_fof3d(ctx: Context, pos: torch.Tensor, box: float, b: float = 0.28, label
     ctx.check(lib().rs_fof3d(ctx.handle, _ptr(pos), _stride_of(pos), n, float(box), float(b), _ptr(labels),
                              C.byref(ng) if want_groups else None, C.byref(nt) if want_tieband else None))
     return labels, (ng.value if want_groups else None), (nt.value if want_tieband else None)
+
+
+def rs_fof3d_accel(ctx: Context, pos: torch.Tensor, box: float, b: float = 0.28, dense_n: int = 16,
+                   labels: torch.Tensor | None = None):
+    """Sec. 3.1, the accelerated variant.  Returns (labels, n_groups,
+    n_centres)."""
+    n = pos.shape[0]
+    if labels is None:
+        labels = torch.empty(n, dtype=torch.int32, device=pos.device)
+    ng, nc = C.c_int64(0), C.c_int64(0)
+    ctx.check(lib().rs_fof3d_accel(ctx.handle, _ptr(pos), _stride_of(pos), n, float(box), float(b), int(dense_n),
+                                   _ptr(labels), C.byref(ng), C.byref(nc)))
+    return labels, ng.value, nc.value
 
 
 def rs_group_sort(ctx: Context, labels: torch.Tensor, min_n: int = 10):

@@ -101,6 +101,77 @@ def test_fof3d_bad_args(rs, ctx):
         rs.rs_fof3d(ctx, pos, 10.0, 0.0)
 
 
+def test_fof3d_narrow_box_without_grid_is_rejected(rs, ctx):
+    """box/l = 7.5: no grid of 4k cells per side has cells between l/2 and
+    l/sqrt(3), so the call fails instead of missing friends three cells
+    apart."""
+    n = 64
+    box = 10.0
+    b = box / 7.5 / n ** (1 / 3)  # l = box / 7.5
+    pos = torch.from_numpy(synth.wrap(np.random.default_rng(75).random((n, 3)) * box, box)).cuda()
+    with pytest.raises(rs.RsError):
+        rs.rs_fof3d(ctx, pos, box, b)
+    b_ok = box / 9.0 / n ** (1 / 3)  # box/l = 9 has one
+    lab, _, _ = rs.rs_fof3d(ctx, pos, box, b_ok)
+    ref, _, _ = oracle.fof3d(pos.cpu().numpy(), box, b_ok)
+    assert np.array_equal(lab.cpu().numpy(), ref)
+
+
+# ---------------------------------------------------------------------------
+# accelerated 3D FOF (Sec. 3.1)
+# ---------------------------------------------------------------------------
+def _accel_check(rs, ctx, pos_np, box, b, dense_n=16):
+    pos = torch.from_numpy(np.ascontiguousarray(pos_np, np.float32)).cuda()
+    lab, ng, nc = rs.rs_fof3d_accel(ctx, pos, box, b, dense_n)
+    ref, _, nref = oracle.fof3d_accel(pos_np, box, b, dense_n=dense_n)
+    lab = lab.cpu().numpy()
+    assert np.array_equal(lab, ref)
+    assert nc == nref and ng == len(np.unique(ref))
+    return lab, nc
+
+
+def test_fof3d_accel_c1_and_small(rs, ctx):
+    for c in (synth.generate("c1"), _small(11), _small(12)):
+        lab, nc = _accel_check(rs, ctx, c.pos, c.box, 0.28)
+        plain, _, _ = oracle.fof3d(c.pos, c.box, 0.28)
+        for g in np.unique(plain)[:2000]:  # groups are unions of plain groups
+            assert len(np.unique(lab[plain == g])) == 1
+        assert nc > 0
+
+
+@pytest.mark.parametrize("dense_n", [0, 3, 16])
+def test_fof3d_accel_dense_uniform(rs, ctx, dense_n):
+    c = synth.uniform(6000, 10.0, 40 + dense_n)
+    _accel_check(rs, ctx, c.pos, c.box, 0.9, dense_n)
+
+
+def test_fof3d_accel_hand_order(rs, ctx):
+    """A dense particle skipped inside the first centre's ball does not join
+    its far satellite; visited first, it does."""
+    rng = np.random.default_rng(2)
+    box, n = 20.0, 20
+    b = 1.0 * n ** (1 / 3) / box  # l = 1
+    v = rng.standard_normal((18, 3))
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    clump = np.array([10.0, 10, 10]) + v * 0.05 * rng.random(18)[:, None]
+    clump[0] = [10.0, 10, 10]
+    k, t = np.array([[10.9, 10, 10]]), np.array([[12.7, 10, 10]])
+    first = synth.wrap(np.vstack([clump, k, t]), box)
+    lab, nc = _accel_check(rs, ctx, first, box, b)
+    assert nc == 1 and lab[18] == 0 and lab[19] == 19
+    second = synth.wrap(np.vstack([k, clump, t]), box)
+    lab2, nc2 = _accel_check(rs, ctx, second, box, b)
+    assert nc2 == 1 and np.all(lab2 == 0)
+
+
+def test_fof3d_accel_bad_args(rs, ctx):
+    pos = torch.from_numpy(synth.wrap(np.random.default_rng(76).random((100, 3)) * 10, 10.0)).cuda()
+    with pytest.raises(rs.RsError):
+        rs.rs_fof3d_accel(ctx, pos, 10.0, 0.28, -1)
+    lab, ng, nc = rs.rs_fof3d_accel(ctx, torch.zeros((0, 3), device="cuda"), 10.0, 0.28)
+    assert lab.numel() == 0 and ng == 0 and nc == 0
+
+
 # ---------------------------------------------------------------------------
 # group CSR
 # ---------------------------------------------------------------------------
@@ -285,6 +356,13 @@ def test_deterministic_repeat(rs, ctx):
 def test_full_path_c2(rs, ctx):
     matched, excused, info = _check_all(rs, ctx, synth.generate("c2"))
     print(f"c2: nodes {info.n_nodes} matched {matched} excused {excused} tie {info.n_tieband}")
+
+
+@pytest.mark.slow
+def test_fof3d_accel_c2(rs, ctx):
+    c = synth.generate("c2")
+    lab, nc = _accel_check(rs, ctx, c.pos, c.box, 0.28)
+    print(f"c2 accelerated FOF: {nc} centres, {len(np.unique(lab))} groups")
 
 
 @pytest.mark.slow
