@@ -154,6 +154,32 @@ def time_oracle_sample(cat, frac_side: float, nn_subset: int = 0, nn_seed: int =
     return len(pos), time.perf_counter() - t0
 
 
+def compare_fof(rsgpu, ctx, pos, box, dense_n, reps=3):
+    """Sec. 3.1: the plain 3D FOF against the paper's accelerated variant,
+    each called alone on the resident workload (one untimed call, then reps
+    timed with CUDA events on the context's stream, which is torch's current
+    stream)."""
+    import torch
+    labels = torch.empty(pos.shape[0], dtype=torch.int32, device=pos.device)
+    calls = (("plain", lambda: rsgpu.rs_fof3d(ctx, pos, box, 0.28, labels=labels, want_groups=True)),
+             ("accel", lambda: rsgpu.rs_fof3d_accel(ctx, pos, box, 0.28, dense_n, labels=labels)))
+    out = {"dense_n": dense_n, "reps": reps}
+    for name, call in calls:
+        r = call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            r = call()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name + "_ms"] = e0.elapsed_time(e1) / reps
+        out[name + "_groups"] = r[1]
+        if name == "accel":
+            out["centres"] = r[2]
+    return out
+
+
 def reference_arm(args, cat, cfg_json):
     """The oracle, as it stands, on host cores: each step one bounded sample."""
     side = args.ref_side
@@ -224,6 +250,8 @@ def main():
     ap.add_argument("--nn-subset", type=int, default=0,
                     help="nodes above this size take l from a random subset of this size (Sec. 3.2; 0: exact)")
     ap.add_argument("--nn-seed", type=int, default=11104372, help="seed of those subsets")
+    ap.add_argument("--fof-accel", type=int, default=None, metavar="DENSE_N",
+                    help="also time the plain 3D FOF against the accelerated variant (Sec. 3.1) alone")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-side", type=float, default=1.0 / 6.0, help="sub-cube side for the CPU baseline")
@@ -346,6 +374,10 @@ def main():
     b_alg = BYTES_FOF_PER_PARTICLE * n + BYTES_LEVEL_PER_MEMBER * stats["sum_level_members"]
     path_frac = b_alg / (ms * 1e-3) / 1e9 / peak
 
+    fof_cmp = None
+    if args.fof_accel is not None:
+        fof_cmp = compare_fof(rsgpu, ctx, pos, cat.box, args.fof_accel)
+
     cpu = None
     if not args.no_cpu_baseline:
         npart, t = time_oracle_sample(cat, args.cpu_side, args.nn_subset, args.nn_seed)
@@ -369,6 +401,8 @@ def main():
                            sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]},
         "stats": stats,
     }
+    if fof_cmp is not None:
+        line["fof3d_compare"] = fof_cmp
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
