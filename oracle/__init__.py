@@ -79,6 +79,12 @@ def _load():
     lib.or_assign.restype = C.c_int
     lib.or_halos_export.argtypes = [P] * 8
     lib.or_leaf_halo.argtypes = [P, P]
+    lib.or_halo_props.argtypes = [P, P, P, P, P, P, P]
+    lib.or_halo_props.restype = C.c_int
+    lib.or_unbind.argtypes = [P, P, P, f64, f64, P, P, P, P]
+    lib.or_unbind.restype = C.c_int
+    lib.or_unbind_set.argtypes = [P, P, f64, P, i64, f64, f64, P, P, P]
+    lib.or_unbind_set.restype = i64
     lib.or_node_dnn.argtypes = [P, P, P, i64, f64, f64, P, P]
     lib.or_node_dnn.restype = f64
     lib.merge_distance.argtypes = [i64, i32, P, P, f64, f64, i64, i32, P, P, f64, f64, f64]
@@ -332,6 +338,71 @@ def assign(tree: Tree, n_total: int, box: float, delta_vir: float = 360.0, nbar:
     leaf = np.empty(tree.n_nodes, np.int32)
     lib.or_leaf_halo(tree.handle, _ptr(leaf))
     return hid, Halos(leaf_halo=leaf, **out)
+
+
+# G in Mpc (km/s)^2 / Msun and the critical density in h^2 Msun / Mpc^3
+G_MPC_KMS2_MSUN = 4.30091e-9
+RHO_CRIT_H2 = 2.77536627e11
+
+
+def particle_gm(nbar: float, omega_m: float = 0.27) -> float:
+    """G times the particle mass, in (km/s)^2 Mpc/h, for a catalogue whose
+    particles sample the matter density Omega_m rho_crit at nbar particles
+    per (Mpc/h)^3 (reading; Omega_m = 0.27 is the Bolshoi cosmology of
+    Sec. 4.1)."""
+    return G_MPC_KMS2_MSUN * omega_m * RHO_CRIT_H2 / nbar
+
+
+def halo_props(tree: Tree, halo_id, halos: "Halos"):
+    """Sec. 3.5.1 centres and the Sec. 3.4 host relation, per halo in the
+    order of :func:`assign`'s Halos: centre node (index into the tree), its
+    level and smallest member, centre xc and velocity vc, assigned particle
+    count and host id (-1 for a host halo)."""
+    lib = _load()
+    H = len(halos.id)
+    halo_id = np.ascontiguousarray(halo_id, np.int32)
+    out = dict(node=np.empty(H, np.int32), xc=np.empty((H, 3)), vc=np.empty((H, 3)),
+               n_assigned=np.empty(H, np.int64), host=np.empty(H, np.int32))
+    st = lib.or_halo_props(tree.handle, _ptr(halo_id), _ptr(out["node"]), _ptr(out["xc"]), _ptr(out["vc"]),
+                           _ptr(out["n_assigned"]), _ptr(out["host"]))
+    if st:
+        raise RuntimeError(f"or_halo_props failed with status {st}")
+    out["level"] = tree.level[out["node"]] if H else np.empty(0, np.int32)
+    out["minidx"] = tree.minidx[out["node"]] if H else np.empty(0, np.int32)
+    return out
+
+
+def unbind(tree: Tree, halo_id, host, gm: float, eps: float = 0.0):
+    """Sec. 3.4 / App. B single-pass unbinding with the exact potential.
+    Per halo: n_part (its particles and its substructure's), n_bound, vbulk;
+    per particle: bound_own (1/0 against its own halo's set, -1 outside every
+    halo)."""
+    lib = _load()
+    H = len(host)
+    halo_id = np.ascontiguousarray(halo_id, np.int32)
+    host = np.ascontiguousarray(host, np.int32)
+    out = dict(n_part=np.empty(H, np.int64), n_bound=np.empty(H, np.int64), vbulk=np.empty((H, 3)),
+               bound_own=np.empty(len(halo_id), np.int8))
+    st = lib.or_unbind(tree.handle, _ptr(halo_id), _ptr(host), float(gm), float(eps), _ptr(out["n_part"]),
+                       _ptr(out["n_bound"]), _ptr(out["vbulk"]), _ptr(out["bound_own"]))
+    if st:
+        raise RuntimeError(f"or_unbind failed with status {st}")
+    return out
+
+
+def unbind_set(pos, vel, box: float, mem, gm: float, eps: float = 0.0):
+    """The bound test on one particle set (App. B with the exact potential):
+    returns (flags, phi per member, bulk velocity)."""
+    pos = _f32(pos)
+    vel = _f32(vel)
+    mem = np.ascontiguousarray(mem, np.int32)
+    n = mem.shape[0]
+    flags = np.empty(n, np.int8)
+    phi = np.empty(n)
+    vb = np.empty(3)
+    _load().or_unbind_set(_ptr(pos), _ptr(vel), float(box), _ptr(mem), n, float(gm), float(eps), _ptr(vb),
+                          _ptr(phi), _ptr(flags))
+    return flags.astype(bool), phi, vb
 
 
 def node_dnn(pos, vel, mem, box: float, f: float = 0.7):

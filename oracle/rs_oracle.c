@@ -22,6 +22,10 @@
  *   or_sample_key    the counter-based generator that draws those subsets
  *   or_assign        seeds, seed merge (Eq. 2), r_dyn,vir (Eq. 4) and the
  *                    hierarchical particle assignment with Eq. 3 (Sec. 3.3)
+ *   or_halo_props    halo centres (Poisson-minimising node, Sec. 3.5.1) and
+ *                    the host/subhalo relation (Sec. 3.4)
+ *   or_unbind        single-pass unbinding with the exact potential
+ *                    (Sec. 3.4, App. B)
  *
  * Readings taken where the paper is silent are written beside the code.
  * Compile with -ffp-contract=off so that no multiply-add is fused and the
@@ -1464,6 +1468,223 @@ void or_halos_export(const or_tree *t, int32_t *id, int64_t *ncore, int32_t *nse
 void or_leaf_halo(const or_tree *t, int32_t *out)
 {
     for (int64_t i = 0; i < t->n_nodes; i++) out[i] = t->halo_id_of_leaf ? t->halo_id_of_leaf[i] : -1;
+}
+
+/* ---- halo centres and the host/subhalo relation (Sec. 3.4, 3.5.1) -------
+ * After the assignment.  Centre (Sec. 3.5.1): among the nodes whose seeds
+ * all belong to the halo (the halo's own part of the hierarchy), the one
+ * whose Poisson error sigma_x / sqrt(n) is smallest; the halo's centre and
+ * velocity are that node's mean position and velocity (reading: the paper's
+ * velocity from the innermost tenth of the halo radius needs the spherical-
+ * overdensity radius, which is not computed here).  Ties go to the node with
+ * the smaller smallest member, then the smaller level.
+ * Host (Sec. 3.4): each halo's centre is treated as a particle and measured
+ * with the metric of Eq. 3 against every halo of the same 3D group with more
+ * assigned particles, using that halo's centre, r_dyn,vir and sigma_v; the
+ * closest is its host (ties to the smaller halo id), none means a host halo.
+ * Outputs are per halo in the order of or_halos_export. */
+typedef struct {
+    int32_t id;
+    int32_t slot;
+} id_slot;
+
+static int cmp_id_slot(const void *a, const void *b)
+{
+    const id_slot *x = (const id_slot *)a, *y = (const id_slot *)b;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+static int32_t slot_of(const id_slot *map, int64_t H, int32_t id)
+{
+    int64_t lo = 0, hi = H;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (map[mid].id < id) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < H && map[lo].id == id) ? map[lo].slot : -1;
+}
+
+static id_slot *halo_map(const or_tree *t)
+{
+    const int64_t H = t->n_halos;
+    id_slot *map = (id_slot *)malloc(sizeof(id_slot) * (size_t)(H > 0 ? H : 1));
+    if (!map) return NULL;
+    for (int64_t h = 0; h < H; h++) {
+        map[h].id = t->h_id[h];
+        map[h].slot = (int32_t)h;
+    }
+    qsort(map, (size_t)H, sizeof(id_slot), cmp_id_slot);
+    return map;
+}
+
+int or_halo_props(const or_tree *t, const int32_t *halo_id, int32_t *centre_node, double *xc, double *vc,
+                  int64_t *n_assigned, int32_t *host)
+{
+    const int64_t NN = t->n_nodes, H = t->n_halos;
+    if (!t->halo_id_of_leaf) return OR_ERR_ARG; /* or_assign first */
+    id_slot *map = halo_map(t);
+    int32_t *pure = (int32_t *)malloc(sizeof(int32_t) * (size_t)(NN > 0 ? NN : 1));
+    int32_t *group = (int32_t *)malloc(sizeof(int32_t) * (size_t)(H > 0 ? H : 1));
+    if (!map || !pure || !group) return OR_ERR_OOM;
+    /* the halo whose seeds fill each node (-1: seeds of several halos);
+     * children come after their parents in the node list */
+    for (int64_t i = 0; i < NN; i++)
+        pure[i] = t->nodes[i].nchild == 0 ? slot_of(map, H, t->halo_id_of_leaf[i]) : -2;
+    for (int64_t i = NN - 1; i >= 0; i--) {
+        const int32_t p = t->nodes[i].parent;
+        if (p < 0) continue;
+        if (pure[p] == -2) pure[p] = pure[i];
+        else if (pure[p] != pure[i]) pure[p] = -1;
+    }
+    for (int64_t h = 0; h < H; h++) centre_node[h] = -1;
+    for (int64_t i = 0; i < NN; i++) {
+        const int32_t h = pure[i];
+        if (h < 0) continue;
+        const or_node *N = &t->nodes[i];
+        const double e = N->sigx * N->sigx / (double)N->count; /* (Poisson error)^2 */
+        const int32_t b = centre_node[h];
+        int better = b < 0;
+        if (!better) {
+            const or_node *B = &t->nodes[b];
+            const double eb = B->sigx * B->sigx / (double)B->count;
+            better = e < eb || (e == eb && (N->minidx < B->minidx || (N->minidx == B->minidx && N->level < B->level)));
+        }
+        if (better) centre_node[h] = (int32_t)i;
+    }
+    for (int64_t h = 0; h < H; h++) {
+        const or_node *N = &t->nodes[centre_node[h]];
+        for (int d = 0; d < 3; d++) {
+            xc[3 * h + d] = N->xbar[d];
+            vc[3 * h + d] = N->vbar[d];
+        }
+        group[h] = N->group;
+        n_assigned[h] = 0;
+    }
+    for (int64_t i = 0; i < t->n_total; i++)
+        if (halo_id[i] >= 0) {
+            const int32_t h = slot_of(map, H, halo_id[i]);
+            if (h >= 0) n_assigned[h]++;
+        }
+    for (int64_t s2 = 0; s2 < H; s2++) {
+        double best = INFINITY;
+        int32_t bid = -1;
+        for (int64_t h = 0; h < H; h++) {
+            if (group[h] != group[s2] || n_assigned[h] <= n_assigned[s2]) continue;
+            double dx2 = 0, dv2 = 0;
+            for (int d = 0; d < 3; d++) {
+                const double dx = min_image(xc[3 * h + d] - xc[3 * s2 + d], t->box);
+                const double dv = vc[3 * h + d] - vc[3 * s2 + d];
+                dx2 += dx * dx;
+                dv2 += dv * dv;
+            }
+            const double d2 = ratio2(dx2, t->h_rdyn2[h]) + ratio2(dv2, t->h_sigv[h] * t->h_sigv[h]);
+            if (d2 < best || (d2 == best && bid >= 0 && t->h_id[h] < bid)) {
+                best = d2;
+                bid = t->h_id[h];
+            }
+        }
+        host[s2] = bid;
+    }
+    free(map);
+    free(pure);
+    free(group);
+    return OR_OK;
+}
+
+/* ---- unbinding (Sec. 3.4, App. B) ----------------------------------------
+ * Single pass.  The particles of a halo for this purpose are those assigned
+ * to it or to any halo below it in the host relation (its substructure);
+ * their mean velocity is the halo's bulk velocity (Sec. 3.5.1).  A particle
+ * is bound to the halo when 1/2 |v - v_bulk|^2 + phi < 0 with the exact
+ * potential per unit mass phi = -Gm sum_j 1 / sqrt(r^2 + eps^2) over the
+ * other particles of the set (periodic minimum image; with eps = 0 a pair at
+ * zero separation is left out).  The paper approximates phi with a tree to
+ * 4% (App. B); this is the direct sum that bounds such an approximation.
+ * Outputs per halo (order of or_halos_export): the set's size, its bound
+ * count and bulk velocity; per particle: bound to its own halo's set (-1 for
+ * particles outside every halo).  host holds each halo's host id or -1. */
+/* The bound test on one particle set mem[0..n): bulk velocity vb (3), the
+ * exact potential per unit mass of every member (phi, optional) and its
+ * flag; returns the number bound. */
+int64_t or_unbind_set(const float *pos, const float *vel, double box, const int32_t *mem, int64_t n, double gm,
+                      double eps, double *vb, double *phi_out, int8_t *flag)
+{
+    const double eps2 = eps * eps;
+    ksum sv[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int64_t a = 0; a < n; a++)
+        for (int d = 0; d < 3; d++) ks_add(&sv[d], (double)vel[3 * mem[a] + d]);
+    for (int d = 0; d < 3; d++) vb[d] = n > 0 ? ks_val(&sv[d]) / (double)n : 0.0;
+    int64_t nb = 0;
+    for (int64_t a = 0; a < n; a++) {
+        const int32_t i = mem[a];
+        ksum phi = {0, 0};
+        for (int64_t b = 0; b < n; b++) {
+            if (b == a) continue;
+            const int32_t j = mem[b];
+            double r2 = 0;
+            for (int d = 0; d < 3; d++) {
+                const double dx = min_image((double)pos[3 * j + d] - (double)pos[3 * i + d], box);
+                r2 += dx * dx;
+            }
+            r2 += eps2;
+            if (r2 > 0) ks_add(&phi, -gm / sqrt(r2));
+        }
+        double ke = 0;
+        for (int d = 0; d < 3; d++) {
+            const double dv = (double)vel[3 * i + d] - vb[d];
+            ke += dv * dv;
+        }
+        if (phi_out) phi_out[a] = ks_val(&phi);
+        flag[a] = (int8_t)(0.5 * ke + ks_val(&phi) < 0);
+        nb += flag[a];
+    }
+    return nb;
+}
+
+int or_unbind(const or_tree *t, const int32_t *halo_id, const int32_t *host, double gm, double eps, int64_t *n_part,
+              int64_t *n_bound, double *vbulk, int8_t *bound_own)
+{
+    const int64_t H = t->n_halos, N = t->n_total;
+    const float *pos = t->pos, *vel = t->vel;
+    id_slot *map = halo_map(t);
+    int32_t *up = (int32_t *)malloc(sizeof(int32_t) * (size_t)(H > 0 ? H : 1));
+    int64_t *off = (int64_t *)calloc((size_t)H + 1, sizeof(int64_t));
+    if (!map || !up || !off) return OR_ERR_OOM;
+    for (int64_t h = 0; h < H; h++) up[h] = host[h] >= 0 ? slot_of(map, H, host[h]) : -1;
+    /* every particle belongs to its halo's set and to each set up the chain */
+    for (int64_t i = 0; i < N; i++) {
+        bound_own[i] = -1;
+        if (halo_id[i] < 0) continue;
+        int64_t guard = 0;
+        for (int32_t h = slot_of(map, H, halo_id[i]); h >= 0 && guard <= H; h = up[h], guard++) off[h + 1]++;
+        if (guard > H) return OR_ERR_ARG; /* the host relation has a cycle */
+    }
+    for (int64_t h = 0; h < H; h++) off[h + 1] += off[h];
+    int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * (size_t)(off[H] > 0 ? off[H] : 1));
+    int64_t *fill = (int64_t *)calloc((size_t)(H > 0 ? H : 1), sizeof(int64_t));
+    if (!mem || !fill) return OR_ERR_OOM;
+    for (int64_t i = 0; i < N; i++) {
+        if (halo_id[i] < 0) continue;
+        for (int32_t h = slot_of(map, H, halo_id[i]); h >= 0; h = up[h]) mem[off[h] + fill[h]++] = (int32_t)i;
+    }
+    int8_t *flags = (int8_t *)malloc((size_t)(off[H] > 0 ? off[H] : 1));
+    if (!flags) return OR_ERR_OOM;
+    for (int64_t h = 0; h < H; h++) {
+        const int32_t *m = mem + off[h];
+        const int64_t n = off[h + 1] - off[h];
+        n_part[h] = n;
+        n_bound[h] = or_unbind_set(pos, vel, t->box, m, n, gm, eps, vbulk + 3 * h, NULL, flags + off[h]);
+        for (int64_t a = 0; a < n; a++)
+            if (slot_of(map, H, halo_id[m[a]]) == (int32_t)h) bound_own[m[a]] = flags[off[h] + a];
+    }
+    free(flags);
+    free(map);
+    free(up);
+    free(off);
+    free(mem);
+    free(fill);
+    return OR_OK;
 }
 
 /* Brute-force nearest-neighbour distances and linking length of one member
