@@ -10,6 +10,8 @@
  *   rs_refine6d    phase-space FOF hierarchy inside every group      Sec. 3.2, Eq. 1
  *   rs_refine6d_sampled  the same with subset linking lengths        Sec. 3.2
  *   rs_assign      seeds, seed merge and particle assignment         Sec. 3.3, Eqs. 2-4
+ *   rs_halo_props  halo centres and the host/subhalo relation        Sec. 3.4, 3.5.1
+ *   rs_unbind      single-pass unbinding                             Sec. 3.4, App. B
  *   rs_find_halos  rs_fof3d, rs_group_sort, rs_refine6d(_sampled) and rs_assign
  *                  in sequence, with host or device buffers
  *
@@ -54,6 +56,7 @@ typedef enum {
 
 typedef struct rs_ctx rs_ctx;
 typedef struct rs_tree rs_tree;
+typedef struct rs_halos rs_halos;
 
 /* Parameters of the method (Table 2 of the paper, plus the merge threshold
  * of Eq. 2 and the virial overdensity of Sec. 3.3). */
@@ -235,6 +238,54 @@ void rs_tree_free(rs_tree *t);
  * n_halos (host, optional) synchronises.  The same pos/vel as rs_refine6d. */
 rs_status rs_assign(rs_ctx *ctx, const rs_tree *t, const float *pos, const float *vel, int32_t stride, int64_t n,
                     double box, const rs_params *params, int32_t *halo_id, int64_t *n_halos);
+
+/* rs_assign that also returns the halos: *halos (optional) receives a
+ * library-owned table (free with rs_halos_free) of every halo's id, centre
+ * and bulk velocity of its seeds' members, sigma_v, r_dyn,vir^2 and 3D
+ * group, and every seed's halo, in the assignment's own halo order.  It is
+ * the input of rs_halo_props and rs_unbind.  Otherwise as rs_assign. */
+rs_status rs_assign_ex(rs_ctx *ctx, const rs_tree *t, const float *pos, const float *vel, int32_t stride, int64_t n,
+                       double box, const rs_params *params, int32_t *halo_id, int64_t *n_halos, rs_halos **halos);
+void rs_halos_free(rs_halos *h);
+/* Number of halos in the table (0 for NULL). */
+int64_t rs_halos_count(const rs_halos *h);
+/* Copies the table's per-halo values to device arrays of n_halos entries
+ * (xbar, vbar: 3 each); any pointer may be NULL. */
+rs_status rs_halos_export(rs_ctx *ctx, const rs_halos *h, int32_t *id, double *xbar, double *vbar, double *sigv,
+                          double *rdyn2);
+
+/* ------------------------------------------------------------------------ */
+/* Halo properties (Sec. 3.4, 3.5.1) and unbinding (Sec. 3.4, App. B)       */
+/* ------------------------------------------------------------------------ */
+/* Centres and hosts, per halo in the table's order (device outputs of
+ * n_halos entries; xc, vc: 3 each).  A node belongs to a halo when all its
+ * seeds do; the halo's centre is the mean position and velocity (xc, vc) of
+ * its node with the smallest sigma_x / sqrt(n) (Sec. 3.5.1; ties: smaller
+ * smallest member, then smaller level), centre_node that node's index.
+ * n_assigned counts the particles with the halo's id in halo_id (device, n,
+ * from the rs_assign_ex that made the table).  host is the id of the halo of
+ * the same 3D group with more assigned particles that is nearest to the
+ * centre under Eq. 3 with that halo's centre, velocity, r_dyn,vir and
+ * sigma_v (Sec. 3.4; ties to the smaller id), or -1.  Synchronises.
+ * RS_ERR_INVALID_ARG if the table is not this tree's or halo_id holds an
+ * id the table lacks. */
+rs_status rs_halo_props(rs_ctx *ctx, const rs_tree *t, const rs_halos *h, const int32_t *halo_id, int64_t n,
+                        int32_t *centre_node, double *xc, double *vc, int64_t *n_assigned, int32_t *host);
+
+/* Single-pass unbinding (Sec. 3.4).  A halo's set is the particles assigned
+ * to it or to any halo below it in the host relation (host: device, n_halos
+ * ids or -1, e.g. from rs_halo_props); v_bulk is the set's mean velocity.  A
+ * particle is bound to the halo when |v - v_bulk|^2 / 2 + phi < 0, with the
+ * potential per unit mass phi = -gm sum_j (r_ij^2 + eps^2)^(-1/2) over the
+ * rest of the set (periodic minimum image; gm = G times the particle mass in
+ * (velocity unit)^2 x (position unit); with eps = 0 coincident pairs are left
+ * out).  phi is summed directly: float32 pair terms, float64 sums of 256-term
+ * chunks.  Device outputs: n_part, n_bound (n_halos int64), vbulk (3 per
+ * halo), bound_own (n int8: bound to its own halo's set; -1 outside every
+ * halo).  Synchronises.  RS_ERR_INVALID_ARG for a cycle in host. */
+rs_status rs_unbind(rs_ctx *ctx, const rs_tree *t, const rs_halos *h, const int32_t *halo_id, const int32_t *host,
+                    const float *pos, const float *vel, int32_t stride, int64_t n, double gm, double eps,
+                    int64_t *n_part, int64_t *n_bound, double *vbulk, int8_t *bound_own);
 
 /* ------------------------------------------------------------------------ */
 /* Whole path                                                                */

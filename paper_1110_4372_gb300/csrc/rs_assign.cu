@@ -13,6 +13,7 @@
 //     nearest, found in float32 with every halo inside a 2^-20 band of the
 //     best re-evaluated in float64 (ties to the smaller halo id).
 #include <cmath>
+#include <new>
 
 #include "rs_refine.cuh"
 
@@ -615,6 +616,35 @@ __global__ void k_as_root_of_rank(AsBufs A, int *root_of_rank)
     if (A.hrank[a] >= 0) root_of_rank[A.hrank[a]] = a;
 }
 
+// per-halo results in rank order, and every seed's halo rank
+__global__ void k_as_export(AsBufs A, NodeArrays nd, int H, const int *root_of_rank, rs_halos out)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= H) return;
+    const int s = root_of_rank[r];
+    out.id[r] = A.hid[s];
+    for (int d = 0; d < 3; d++) {
+        out.xbar[3 * r + d] = A.hx[3 * s + d];
+        out.vbar[3 * r + d] = A.hv[3 * s + d];
+    }
+    out.sigv[r] = A.hsigv[s];
+    out.rdyn2[r] = A.hrdyn2[s];
+    out.root[r] = nd.root[A.leaf_node[s]];
+}
+
+__global__ void k_as_export_leaf(AsBufs A, const int *leaf_root, int *leaf_halo)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= A.L) return;
+    leaf_halo[A.leaf_node[a]] = A.hrank[leaf_root[a]];
+}
+
+rs_status empty_halos(rs_halos **out)
+{
+    *out = new (std::nothrow) rs_halos();
+    return *out ? RS_OK : RS_ERR_OOM;
+}
+
 template <typename T>
 T *carve(char *&p, int64_t count)
 {
@@ -670,10 +700,12 @@ rs_status large_rdyn(rs_ctx *ctx, AsBufs A, int H, const int *root_of_rank, cons
 
 }  // namespace
 
-extern "C" rs_status rs_assign(rs_ctx *ctx, const rs_tree *t, const float *pos, const float *vel, int32_t stride,
-                               int64_t n, double box, const rs_params *params, int32_t *halo_id, int64_t *n_halos)
+extern "C" rs_status rs_assign_ex(rs_ctx *ctx, const rs_tree *t, const float *pos, const float *vel, int32_t stride,
+                                  int64_t n, double box, const rs_params *params, int32_t *halo_id, int64_t *n_halos,
+                                  rs_halos **halos_out)
 {
     if (!ctx) return RS_ERR_INVALID_ARG;
+    if (halos_out) *halos_out = nullptr;
     if (!t || !params || n < 0 || (stride != 3 && stride != 4) || !(box > 0) || (n > 0 && (!pos || !vel || !halo_id)))
         return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_assign: bad argument");
     if (n != t->n_total) return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_assign: n differs from the tree's");
@@ -681,7 +713,7 @@ extern "C" rs_status rs_assign(rs_ctx *ctx, const rs_tree *t, const float *pos, 
         return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_assign: delta_vir and merge_thresh must be positive");
     if (n == 0) {
         if (n_halos) *n_halos = 0;
-        return RS_OK;
+        return halos_out ? empty_halos(halos_out) : RS_OK;
     }
     const double nbar = params->nbar > 0 ? params->nbar : (double)n / (box * box * box);
     const double rho_term = (4.0 / 3.0) * M_PI * params->delta_vir * nbar;
@@ -692,7 +724,7 @@ extern "C" rs_status rs_assign(rs_ctx *ctx, const rs_tree *t, const float *pos, 
               halo_id, n, -1);
     if (nn == 0) {
         if (n_halos) *n_halos = 0;
-        return RS_OK;
+        return halos_out ? empty_halos(halos_out) : RS_OK;
     }
     // seeds
     RS_WS(ctx, unsigned, fl, WS_AS_0, 2 * (int64_t)nn + 8);
@@ -802,9 +834,65 @@ extern "C" rs_status rs_assign(rs_ctx *ctx, const rs_tree *t, const float *pos, 
     RS_LAUNCH(ctx, "as_assign", k_as_assign, T, AS_THREADS, 0, A, nd, (const int *)leaf_root, (const int *)cand_g,
               (const int *)node_la, (const int64_t *)coff, (const int *)ncand, (const int *)tt, (const int *)(tt + T),
               (const int *)t->members, pos, vel, stride, box, boxf, halo_id, ctx->d_status);
+    if (halos_out) {
+        rs_halos *hs = new (std::nothrow) rs_halos();
+        if (!hs) return RS_ERR_OOM;
+        hs->n_halos = H;
+        hs->n_nodes = nn;
+        const size_t bytes = (size_t)(H + 1) * (4 + 48 + 8 + 8 + 4) + (size_t)(nn + 1) * 4 + 8 * 256;
+        if (cudaMalloc(&hs->block, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            delete hs;
+            return rs_fail(ctx, RS_ERR_OOM, "rs_assign: halo table allocation failed");
+        }
+        char *b = (char *)hs->block;
+        hs->id = carve<int>(b, H);
+        hs->xbar = carve<double>(b, 3 * H);
+        hs->vbar = carve<double>(b, 3 * H);
+        hs->sigv = carve<double>(b, H);
+        hs->rdyn2 = carve<double>(b, H);
+        hs->root = carve<int>(b, H);
+        hs->leaf_halo = carve<int>(b, nn);
+        RS_LAUNCH(ctx, "as_export_fill", k_fill_i32v, ceil_div(nn, 256), 256, 0, (int32_t *)hs->leaf_halo, (int64_t)nn,
+                  -1);
+        if (H > 0)
+            RS_LAUNCH(ctx, "as_export", k_as_export, ceil_div(H, 256), 256, 0, A, nd, (int)H,
+                      (const int *)root_of_rank, *hs);
+        RS_LAUNCH(ctx, "as_export_leaf", k_as_export_leaf, gl, 256, 0, A, (const int *)leaf_root, hs->leaf_halo);
+        *halos_out = hs;
+    }
     if (n_halos) {
         *n_halos = H;
         RS_TRY(rs_sync_check(ctx, "rs_assign"));
     }
+    return RS_OK;
+}
+
+extern "C" rs_status rs_assign(rs_ctx *ctx, const rs_tree *t, const float *pos, const float *vel, int32_t stride,
+                               int64_t n, double box, const rs_params *params, int32_t *halo_id, int64_t *n_halos)
+{
+    return rs_assign_ex(ctx, t, pos, vel, stride, n, box, params, halo_id, n_halos, nullptr);
+}
+
+extern "C" void rs_halos_free(rs_halos *h)
+{
+    if (!h) return;
+    if (h->block) cudaFree(h->block);
+    delete h;
+}
+
+extern "C" int64_t rs_halos_count(const rs_halos *h) { return h ? h->n_halos : 0; }
+
+extern "C" rs_status rs_halos_export(rs_ctx *ctx, const rs_halos *h, int32_t *id, double *xbar, double *vbar,
+                                     double *sigv, double *rdyn2)
+{
+    if (!ctx || !h) return RS_ERR_INVALID_ARG;
+    const size_t H = (size_t)h->n_halos;
+    if (H == 0) return RS_OK;
+    if (id) RS_CUDA(ctx, cudaMemcpyAsync(id, h->id, 4 * H, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (xbar) RS_CUDA(ctx, cudaMemcpyAsync(xbar, h->xbar, 24 * H, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (vbar) RS_CUDA(ctx, cudaMemcpyAsync(vbar, h->vbar, 24 * H, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (sigv) RS_CUDA(ctx, cudaMemcpyAsync(sigv, h->sigv, 8 * H, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (rdyn2) RS_CUDA(ctx, cudaMemcpyAsync(rdyn2, h->rdyn2, 8 * H, cudaMemcpyDeviceToDevice, ctx->stream));
     return RS_OK;
 }

@@ -27,6 +27,20 @@ struct rs_tree {
     void *block = nullptr;   // single device allocation holding everything
 };
 
+// Per-halo results of the assignment, kept for the halo-property steps
+// (Sec. 3.4, 3.5.1).  Halos are in the assignment's rank order.
+struct rs_halos {
+    int64_t n_halos = 0, n_nodes = 0;
+    int *id = nullptr;         // halo id: smallest particle index of its seeds
+    double *xbar = nullptr;    // 3 per halo: centre of the seeds' members
+    double *vbar = nullptr;    // 3 per halo
+    double *sigv = nullptr;    // velocity dispersion of the seeds' members
+    double *rdyn2 = nullptr;   // r_dyn,vir^2 (Eq. 4)
+    int *root = nullptr;       // root node of the halo's 3D group
+    int *leaf_halo = nullptr;  // per tree node: the halo of a seed, -1 for inner nodes
+    void *block = nullptr;
+};
+
 // Fixed-point scale of the exact moment sums: positions and velocities are
 // rounded to multiples of 2^-32 (of their units) before summation.
 #define RS_FX 4294967296.0f

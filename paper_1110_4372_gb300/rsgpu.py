@@ -68,6 +68,13 @@ def _declare(lib):
         "rs_tree_level_labels": (C.c_int, [P, P, i32, i64, P]),
         "rs_tree_free": (None, [P]),
         "rs_assign": (C.c_int, [P, P, P, P, i32, i64, f64, C.POINTER(rs_params), P, C.POINTER(i64)]),
+        "rs_assign_ex": (C.c_int, [P, P, P, P, i32, i64, f64, C.POINTER(rs_params), P, C.POINTER(i64),
+                                   C.POINTER(P)]),
+        "rs_halos_free": (None, [P]),
+        "rs_halos_count": (i64, [P]),
+        "rs_halos_export": (C.c_int, [P, P, P, P, P, P, P]),
+        "rs_halo_props": (C.c_int, [P, P, P, P, i64, P, P, P, P, P]),
+        "rs_unbind": (C.c_int, [P, P, P, P, P, P, P, i32, i64, f64, f64, P, P, P, P]),
         "rs_find_halos": (C.c_int, [P, P, P, i32, i64, f64, C.POINTER(rs_params), P, P, C.POINTER(rs_stats),
                                     i32]),
         "rs_profile_enable": (C.c_int, [P, i32]),
@@ -293,6 +300,81 @@ def rs_assign(ctx: Context, tree: Tree, pos: torch.Tensor, vel: torch.Tensor, bo
     ctx.check(lib().rs_assign(ctx.handle, tree.handle, _ptr(pos), _ptr(vel), _stride_of(pos), n, float(box),
                               C.byref(p), _ptr(halo_id), C.byref(nh)))
     return halo_id, nh.value
+
+
+class Halos:
+    """Library-owned per-halo table from :func:`rs_assign_ex`."""
+
+    def __init__(self, ctx: Context, handle: C.c_void_p, device):
+        self.ctx, self._h, self.device = ctx, handle, device
+        self.n = int(lib().rs_halos_count(handle))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def arrays(self) -> dict:
+        """id, xbar, vbar, sigv, rdyn2 as device tensors (the table's order)."""
+        H = self.n
+        out = dict(id=torch.empty(H, dtype=torch.int32, device=self.device),
+                   xbar=torch.empty((H, 3), dtype=torch.float64, device=self.device),
+                   vbar=torch.empty((H, 3), dtype=torch.float64, device=self.device),
+                   sigv=torch.empty(H, dtype=torch.float64, device=self.device),
+                   rdyn2=torch.empty(H, dtype=torch.float64, device=self.device))
+        if H:
+            self.ctx.check(lib().rs_halos_export(self.ctx.handle, self._h, *[_ptr(out[k]) for k in
+                                                                          ("id", "xbar", "vbar", "sigv", "rdyn2")]))
+        return out
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib().rs_halos_free(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+def rs_assign_ex(ctx: Context, tree: Tree, pos: torch.Tensor, vel: torch.Tensor, box: float,
+                 p: rs_params | None = None):
+    """Sec. 3.3 with the per-halo table.  Returns (halo_id, Halos)."""
+    p = p or params()
+    n = pos.shape[0]
+    halo_id = torch.empty(n, dtype=torch.int32, device=pos.device)
+    nh = C.c_int64(0)
+    h = C.c_void_p()
+    ctx.check(lib().rs_assign_ex(ctx.handle, tree.handle, _ptr(pos), _ptr(vel), _stride_of(pos), n, float(box),
+                                 C.byref(p), _ptr(halo_id), C.byref(nh), C.byref(h)))
+    return halo_id, Halos(ctx, h, pos.device)
+
+
+def rs_halo_props(ctx: Context, tree: Tree, halos: Halos, halo_id: torch.Tensor) -> dict:
+    """Sec. 3.5.1 centres and the Sec. 3.4 host relation, per halo in the
+    table's order: centre_node, xc, vc, n_assigned, host (device tensors)."""
+    H, dev = halos.n, halo_id.device
+    out = dict(centre_node=torch.empty(H, dtype=torch.int32, device=dev),
+               xc=torch.empty((H, 3), dtype=torch.float64, device=dev),
+               vc=torch.empty((H, 3), dtype=torch.float64, device=dev),
+               n_assigned=torch.empty(H, dtype=torch.int64, device=dev),
+               host=torch.empty(H, dtype=torch.int32, device=dev))
+    ctx.check(lib().rs_halo_props(ctx.handle, tree.handle, halos.handle, _ptr(halo_id), halo_id.shape[0],
+                                  *[_ptr(out[k]) for k in ("centre_node", "xc", "vc", "n_assigned", "host")]))
+    return out
+
+
+def rs_unbind(ctx: Context, tree: Tree, halos: Halos, halo_id: torch.Tensor, host: torch.Tensor, pos: torch.Tensor,
+              vel: torch.Tensor, gm: float, eps: float = 0.0) -> dict:
+    """Sec. 3.4 / App. B single-pass unbinding: n_part, n_bound, vbulk per
+    halo and bound_own per particle (device tensors)."""
+    H, dev, n = halos.n, pos.device, pos.shape[0]
+    out = dict(n_part=torch.empty(H, dtype=torch.int64, device=dev),
+               n_bound=torch.empty(H, dtype=torch.int64, device=dev),
+               vbulk=torch.empty((H, 3), dtype=torch.float64, device=dev),
+               bound_own=torch.empty(n, dtype=torch.int8, device=dev))
+    ctx.check(lib().rs_unbind(ctx.handle, tree.handle, halos.handle, _ptr(halo_id), _ptr(host), _ptr(pos),
+                              _ptr(vel), _stride_of(pos), n, float(gm), float(eps),
+                              *[_ptr(out[k]) for k in ("n_part", "n_bound", "vbulk", "bound_own")]))
+    return out
 
 
 def rs_find_halos(ctx: Context, pos: torch.Tensor, vel: torch.Tensor, box: float, p: rs_params | None = None,
