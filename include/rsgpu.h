@@ -279,13 +279,20 @@ rs_status rs_halo_props(rs_ctx *ctx, const rs_tree *t, const rs_halos *h, const 
  * potential per unit mass phi = -gm sum_j (r_ij^2 + eps^2)^(-1/2) over the
  * rest of the set (periodic minimum image; gm = G times the particle mass in
  * (velocity unit)^2 x (position unit); with eps = 0 coincident pairs are left
- * out).  phi is summed directly: float32 pair terms, float64 sums of 256-term
- * chunks.  Device outputs: n_part, n_bound (n_halos int64), vbulk (3 per
- * halo), bound_own (n int8: bound to its own halo's set; -1 outside every
- * halo).  Synchronises.  RS_ERR_INVALID_ARG for a cycle in host. */
+ * out).  theta = 0: phi is summed directly for every set (float32 pair terms,
+ * float64 sums of 256-term chunks).  0 < theta < 1: sets above 4096 members
+ * use a tree in which a box of particles with mass centre x0, sigma^2 and
+ * r_max stands for them beyond d(theta) = r_max/2 + sqrt((r_max/2)^2 +
+ * sigma^2/theta) (App. B; the paper's accuracy is 4%), so each such phi is
+ * within theta |phi| of the direct sum.  Device outputs: n_part, n_bound
+ * (n_halos int64), vbulk (3 per halo), bound_own (n int8: bound to its own
+ * halo's set; -1 outside every halo), phi_own (optional, n float64: phi in
+ * its own halo's set; untouched outside every halo).  Synchronises.
+ * RS_ERR_INVALID_ARG for a cycle in host or theta outside [0, 1). */
 rs_status rs_unbind(rs_ctx *ctx, const rs_tree *t, const rs_halos *h, const int32_t *halo_id, const int32_t *host,
                     const float *pos, const float *vel, int32_t stride, int64_t n, double gm, double eps,
-                    int64_t *n_part, int64_t *n_bound, double *vbulk, int8_t *bound_own);
+                    double theta, int64_t *n_part, int64_t *n_bound, double *vbulk, int8_t *bound_own,
+                    double *phi_own);
 
 /* ------------------------------------------------------------------------ */
 /* Whole path                                                                */

@@ -14,12 +14,20 @@
 //
 // Unbinding.  A halo's set is its own particles and those of every halo
 // below it in the host relation.  Sets are gathered as (set, particle) keys
-// and radix-sorted, so each set is a contiguous run in particle order.  The
-// bulk velocity is a float64 block reduction; the potential per unit mass is
-// a direct sum over the set, one CTA per 256 targets with the sources staged
-// through shared memory, float32 pair terms added per 256-source chunk and
-// the chunk sums accumulated in float64.  Periodic differences take the
-// far-side coordinate minus the box first (exact for x >= box/2).
+// and radix-sorted, so each set is a contiguous run.  The bulk velocity is a
+// float64 block reduction.  The potential per unit mass is either a direct
+// sum over the set (one CTA per 256 targets, sources staged through shared
+// memory, float32 pair terms added per 256-source chunk, chunk sums in
+// float64), or, for sets above UB_DIRECT_MAX members when theta > 0, a tree
+// walk (App. B): each set is put in Morton order of its unwrapped positions,
+// cut into 32-member leaves under a 32-ary box hierarchy whose boxes keep
+// their mass centre x0, sigma^2 = mean |x - x0|^2 and r_max; a box stands for
+// its particles (monopole) beyond d(theta) = r_max/2 + sqrt((r_max/2)^2 +
+// sigma^2/theta) from x0, which bounds the relative error of each accepted
+// term, hence of the sum, by theta (Salmon & Warren 1994).  One warp walks
+// the tree for the 32 targets of a leaf, accepting a box only when the whole
+// leaf lies beyond d(theta).  Periodic differences take the far-side
+// coordinate minus the box first (exact for x >= box/2).
 #include <cmath>
 #include <new>
 
@@ -28,7 +36,12 @@
 namespace {
 
 constexpr int HP_THREADS = 256;
-constexpr int UB_TILE = 256;  // targets per CTA and sources per shared-memory chunk
+constexpr int UB_TILE = 256;          // targets per CTA and sources per shared-memory chunk
+constexpr int UB_DIRECT_MAX = 4096;   // sets up to this size are summed directly
+constexpr int UT_LEAF = 32;           // members per leaf, children per box
+constexpr int UT_WARPS = 8;           // warps per CTA in the tree walk
+constexpr int UT_STACK = 256;         // boxes on a warp's stack
+constexpr int UT_MAX_LEVELS = 8;      // 32^8 > 2^31 members
 
 __global__ void k_hp_init(NodeArrays nd, int nn, const int *leaf_halo, int *pure)
 {
@@ -269,11 +282,15 @@ __global__ void __launch_bounds__(HP_THREADS) k_ub_bulk(int H, const int64_t *of
     }
 }
 
-__global__ void k_ub_tiles(int H, const int64_t *off, int64_t *tiles)
+__device__ __forceinline__ bool ub_tree_set(int64_t n, int tree_on) { return tree_on && n > UB_DIRECT_MAX; }
+
+// direct-sum tiles of every set summed directly
+__global__ void k_ub_tiles(int H, const int64_t *off, int tree_on, int64_t *tiles)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= H) return;
-    tiles[r] = (off[r + 1] - off[r] + UB_TILE - 1) / UB_TILE;
+    const int64_t n = off[r + 1] - off[r];
+    tiles[r] = ub_tree_set(n, tree_on) ? 0 : (n + UB_TILE - 1) / UB_TILE;
 }
 
 __global__ void k_ub_npart(int H, const int64_t *off, int64_t *n_part)
@@ -303,12 +320,32 @@ __device__ __forceinline__ float pdiff(float a, float b, float box)
     return d;
 }
 
+// the bound test of particle i in set r, given its potential per unit mass
+__device__ __forceinline__ void ub_finish(uint32_t i, int r, double phi, const float *vel, int stride,
+                                          const double *vbulk, const int32_t *halo_id, const int *hid,
+                                          unsigned long long *n_bound, int8_t *bound_own, double *phi_own)
+{
+    const float *vi = vel + (int64_t)stride * i;
+    double ke = 0;
+    for (int d = 0; d < 3; d++) {
+        const double dv = (double)vi[d] - vbulk[3 * r + d];
+        ke += dv * dv;
+    }
+    const bool bound = 0.5 * ke + phi < 0.0;
+    if (bound) atomicAdd(&n_bound[r], 1ull);
+    if (halo_id[i] == hid[r]) {
+        bound_own[i] = bound ? 1 : 0;
+        if (phi_own) phi_own[i] = phi;
+    }
+}
+
 // potential and bound flag of every member of a set tile
 __global__ void __launch_bounds__(UB_TILE) k_ub_phi(const int *trank, const int *tq0, const int64_t *off,
                                                     const uint32_t *mem, const float *pos, const float *vel,
                                                     int stride, float boxf, double gm, float eps2f,
                                                     const double *vbulk, const int32_t *halo_id, const int *hid,
-                                                    unsigned long long *n_bound, int8_t *bound_own)
+                                                    unsigned long long *n_bound, int8_t *bound_own,
+                                                    double *phi_own)
 {
     __shared__ float4 src[UB_TILE];
     const int r = trank[blockIdx.x];
@@ -341,16 +378,339 @@ __global__ void __launch_bounds__(UB_TILE) k_ub_phi(const int *trank, const int 
         __syncthreads();
     }
     if (!mine) return;
-    phi *= gm;
-    const float *vi = vel + (int64_t)stride * i;
-    double ke = 0;
-    for (int d = 0; d < 3; d++) {
-        const double dv = (double)vi[d] - vbulk[3 * r + d];
-        ke += dv * dv;
+    ub_finish(i, r, phi * gm, vel, stride, vbulk, halo_id, hid, n_bound, bound_own, phi_own);
+}
+
+// ---- tree walk for large sets ----
+// Boxes of one set: level 0 holds the leaves (32 consecutive members in
+// Morton order), level h the boxes over 32 consecutive boxes of level h-1,
+// up to one root; levels are stored one after another from level 0.
+struct UTView {
+    int H;                   // levels
+    int cnt[UT_MAX_LEVELS];  // boxes per level
+    int off[UT_MAX_LEVELS];  // first box of each level
+};
+
+__device__ __forceinline__ void ut_view(UTView &V, int64_t n)
+{
+    int c = (int)((n + UT_LEAF - 1) / UT_LEAF), o = 0, h = 0;
+    for (;;) {
+        V.cnt[h] = c;
+        V.off[h] = o;
+        o += c;
+        h++;
+        if (c == 1 || h == UT_MAX_LEVELS) break;
+        c = (c + UT_LEAF - 1) / UT_LEAF;
     }
-    const bool bound = 0.5 * ke + phi < 0.0;
-    if (bound) atomicAdd(&n_bound[r], 1ull);
-    if (halo_id[i] == hid[r]) bound_own[i] = bound ? 1 : 0;
+    V.H = h;
+}
+
+__device__ __forceinline__ int64_t ut_boxes(int64_t n)
+{
+    int64_t c = (n + UT_LEAF - 1) / UT_LEAF, t = 0;
+    for (;;) {
+        t += c;
+        if (c == 1) break;
+        c = (c + UT_LEAF - 1) / UT_LEAF;
+    }
+    return t;
+}
+
+// a box: mass centre and count (c), sigma^2, r_max and the opening distance (s)
+struct UBoxes {
+    float4 *c;
+    float4 *s;
+};
+
+__global__ void k_ub_ref(int H, const int64_t *off, const uint32_t *mem, const float *pos, int stride, float4 *ref)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= H || off[r + 1] == off[r]) return;
+    const float *p = pos + (int64_t)stride * mem[off[r]];
+    ref[r] = make_float4(p[0], p[1], p[2], 0.f);
+}
+
+// positions relative to the set's first member, nearest periodic image
+__global__ void k_ub_upos(int64_t total, const uint64_t *keys, const uint32_t *mem, const float *pos, int stride,
+                          const float4 *ref, float boxf, float4 *upos)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    const int r = (int)(keys[k] >> 32);
+    const uint32_t i = mem[k];
+    const float *p = pos + (int64_t)stride * i;
+    const float4 a = ref[r];
+    upos[k] = make_float4(pdiff(a.x, p[0], boxf), pdiff(a.y, p[1], boxf), pdiff(a.z, p[2], boxf),
+                          __int_as_float((int)i));
+}
+
+// bounding cube of every tree set: lower corner and 1024 / side
+__global__ void __launch_bounds__(HP_THREADS) k_ub_bbox(int H, const int64_t *off, int tree_on, const float4 *upos,
+                                                        float4 *cube)
+{
+    __shared__ float lo[3][HP_THREADS], hi[3][HP_THREADS];
+    for (int r = blockIdx.x; r < H; r += gridDim.x) {
+        const int64_t a = off[r], b = off[r + 1];
+        if (!ub_tree_set(b - a, tree_on)) continue;  // uniform over the block
+        float l[3] = {INFINITY, INFINITY, INFINITY}, u[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t k = a + threadIdx.x; k < b; k += HP_THREADS) {
+            const float4 p = upos[k];
+            l[0] = fminf(l[0], p.x);
+            l[1] = fminf(l[1], p.y);
+            l[2] = fminf(l[2], p.z);
+            u[0] = fmaxf(u[0], p.x);
+            u[1] = fmaxf(u[1], p.y);
+            u[2] = fmaxf(u[2], p.z);
+        }
+        for (int d = 0; d < 3; d++) {
+            lo[d][threadIdx.x] = l[d];
+            hi[d][threadIdx.x] = u[d];
+        }
+        __syncthreads();
+        for (int w = HP_THREADS / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w)
+                for (int d = 0; d < 3; d++) {
+                    lo[d][threadIdx.x] = fminf(lo[d][threadIdx.x], lo[d][threadIdx.x + w]);
+                    hi[d][threadIdx.x] = fmaxf(hi[d][threadIdx.x], hi[d][threadIdx.x + w]);
+                }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const float side = fmaxf(fmaxf(hi[0][0] - lo[0][0], hi[1][0] - lo[1][0]), hi[2][0] - lo[2][0]);
+            cube[r] = make_float4(lo[0][0], lo[1][0], lo[2][0], side > 0.f ? 1024.f / side : 0.f);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v)
+{
+    v &= 1023u;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t cell10(float x, float lo, float scale)
+{
+    const float q = (x - lo) * scale;
+    return q <= 0.f ? 0u : (q >= 1023.f ? 1023u : (uint32_t)q);
+}
+
+// (set, Morton code) keys of every entry; sets summed directly keep code 0
+__global__ void k_ub_morton(int64_t total, const uint64_t *keys, const int64_t *off, int tree_on, const float4 *upos,
+                            const float4 *cube, uint64_t *mkeys, uint32_t *mvals)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    const int r = (int)(keys[k] >> 32);
+    uint32_t code = 0;
+    if (ub_tree_set(off[r + 1] - off[r], tree_on)) {
+        const float4 c = cube[r], p = upos[k];
+        code = (spread10(cell10(p.z, c.z, c.w)) << 2) | (spread10(cell10(p.y, c.y, c.w)) << 1) |
+               spread10(cell10(p.x, c.x, c.w));
+    }
+    mkeys[k] = ((uint64_t)(uint32_t)r << 30) | code;
+    mvals[k] = (uint32_t)k;
+}
+
+__global__ void k_ub_gather(int64_t total, const uint32_t *perm, const float4 *upos, const uint32_t *mem,
+                            float4 *tpos, uint32_t *tmem)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    const uint32_t s = perm[k];
+    tpos[k] = upos[s];
+    tmem[k] = mem[s];
+}
+
+// boxes and leaves of every set (zero for sets summed directly)
+__global__ void k_ub_boxcount(int H, const int64_t *off, int tree_on, int64_t *nbox, int64_t *nleaf)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= H) return;
+    const int64_t n = off[r + 1] - off[r];
+    const bool t = ub_tree_set(n, tree_on);
+    nbox[r] = t ? ut_boxes(n) : 0;
+    nleaf[r] = t ? (n + UT_LEAF - 1) / UT_LEAF : 0;
+}
+
+__global__ void k_ub_leafjobs(int H, const int64_t *loff, int *jset, int *jleaf)
+{
+    const int r = blockIdx.x;
+    if (r >= H) return;
+    for (int64_t j = loff[r] + threadIdx.x; j < loff[r + 1]; j += blockDim.x) {
+        jset[j] = r;
+        jleaf[j] = (int)(j - loff[r]);
+    }
+}
+
+__device__ __forceinline__ float ut_dopen(float sig2, float rmax, float theta)
+{
+    const float h = 0.5f * rmax;
+    return h + sqrtf(h * h + sig2 / theta);
+}
+
+// leaf boxes: one warp per leaf, a member per lane
+__global__ void __launch_bounds__(UT_WARPS * 32) k_ub_leafbox(int64_t njobs, const int *jset, const int *jleaf,
+                                                             const int64_t *off, const int64_t *bbase,
+                                                             const float4 *tpos, float theta, UBoxes B)
+{
+    const int64_t j = (int64_t)blockIdx.x * UT_WARPS + warp_id();
+    if (j >= njobs) return;
+    const int lane = lane_id();
+    const int r = jset[j], leaf = jleaf[j];
+    const int64_t a = off[r], n = off[r + 1] - a;
+    const int64_t m = (int64_t)leaf * UT_LEAF + lane;
+    const bool have = m < n;
+    const float4 p = have ? tpos[a + m] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float cnt = warp_sum(have ? 1.f : 0.f);
+    const float x0 = warp_sum(have ? p.x : 0.f) / cnt, y0 = warp_sum(have ? p.y : 0.f) / cnt,
+                z0 = warp_sum(have ? p.z : 0.f) / cnt;
+    const float dx = p.x - x0, dy = p.y - y0, dz = p.z - z0;
+    const float d2 = have ? dx * dx + dy * dy + dz * dz : 0.f;
+    const float sig2 = warp_sum(d2) / cnt;
+    float rm = sqrtf(d2);
+    for (int o = 16; o > 0; o >>= 1) rm = fmaxf(rm, __shfl_xor_sync(0xffffffffu, rm, o));
+    if (lane == 0) {
+        const int64_t b = bbase[r] + leaf;
+        B.c[b] = make_float4(x0, y0, z0, cnt);
+        B.s[b] = make_float4(sig2, rm, ut_dopen(sig2, rm, theta), 0.f);
+    }
+}
+
+// upper levels of every tree set, one block per set (parallel-axis sums for
+// sigma^2; r_max bounded by the children's distance plus their r_max)
+__global__ void __launch_bounds__(HP_THREADS) k_ub_upper(int H, const int64_t *off, int tree_on,
+                                                         const int64_t *bbase, float theta, UBoxes B)
+{
+    for (int r = blockIdx.x; r < H; r += gridDim.x) {
+        const int64_t n = off[r + 1] - off[r];
+        if (!ub_tree_set(n, tree_on)) continue;  // uniform over the block
+        UTView V;
+        ut_view(V, n);
+        const int64_t base = bbase[r];
+        for (int h = 1; h < V.H; h++) {
+            for (int b = threadIdx.x; b < V.cnt[h]; b += HP_THREADS) {
+                const int c0 = b * UT_LEAF, c1 = min(c0 + UT_LEAF, V.cnt[h - 1]);
+                float cnt = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+                for (int c = c0; c < c1; c++) {
+                    const float4 q = B.c[base + V.off[h - 1] + c];
+                    cnt += q.w;
+                    sx += q.w * q.x;
+                    sy += q.w * q.y;
+                    sz += q.w * q.z;
+                }
+                const float x0 = sx / cnt, y0 = sy / cnt, z0 = sz / cnt;
+                float s2 = 0.f, rm = 0.f;
+                for (int c = c0; c < c1; c++) {
+                    const float4 q = B.c[base + V.off[h - 1] + c];
+                    const float4 w = B.s[base + V.off[h - 1] + c];
+                    const float dx = q.x - x0, dy = q.y - y0, dz = q.z - z0;
+                    const float g2 = dx * dx + dy * dy + dz * dz;
+                    s2 += q.w * (w.x + g2);
+                    rm = fmaxf(rm, sqrtf(g2) + w.y);
+                }
+                s2 /= cnt;
+                B.c[base + V.off[h] + b] = make_float4(x0, y0, z0, cnt);
+                B.s[base + V.off[h] + b] = make_float4(s2, rm, ut_dopen(s2, rm, theta), 0.f);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// tree walk: one warp per leaf of targets, a target per lane
+__global__ void __launch_bounds__(UT_WARPS * 32) k_ub_walk(int64_t njobs, const int *jset, const int *jleaf,
+                                                          const int64_t *off, const int64_t *bbase,
+                                                          const float4 *tpos, const uint32_t *tmem, UBoxes B,
+                                                          double gm, float eps2f, const float *vel, int stride,
+                                                          const double *vbulk, const int32_t *halo_id, const int *hid,
+                                                          unsigned long long *n_bound, int8_t *bound_own,
+                                                          double *phi_own, rs_dev_status *st)
+{
+    __shared__ int stk[UT_WARPS][UT_STACK];
+    const unsigned FULL = 0xffffffffu;
+    const int64_t j = (int64_t)blockIdx.x * UT_WARPS + warp_id();
+    if (j >= njobs) return;
+    const int w = warp_id(), lane = lane_id();
+    const int r = jset[j], leaf = jleaf[j];
+    const int64_t a = off[r], n = off[r + 1] - a;
+    UTView V;
+    ut_view(V, n);
+    const int64_t base = bbase[r];
+    const int64_t m = (int64_t)leaf * UT_LEAF + lane;
+    const bool have = m < n;
+    const float4 t = have ? tpos[a + m] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t ti = (uint32_t)__float_as_int(t.w);
+    // the group: this leaf's centre and radius
+    const float4 gc = B.c[base + leaf], gs = B.s[base + leaf];
+    float acc = 0.f;    // current chunk of terms
+    double phi = 0.0;   // chunks
+    int terms = 0;
+    int *S = stk[w];
+    if (lane == 0) S[0] = ((V.H - 1) << 24) | 0;  // the root
+    int sp = 1;
+    __syncwarp();
+    for (int it = 0; sp > 0 && it < (1 << 24); it++) {
+        sp--;
+        const int ent = S[sp];
+        __syncwarp();
+        const int h = ent >> 24, b = ent & 0xffffff;
+        if (h == 0) {  // a leaf: every member directly
+            const int64_t l0 = (int64_t)b * UT_LEAF;
+            const int64_t mm = l0 + lane;
+            const float4 q = mm < n ? tpos[a + mm] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int cnt = (int)(n - l0 < UT_LEAF ? n - l0 : UT_LEAF);
+            for (int k = 0; k < cnt; k++) {
+                const float qx = __shfl_sync(FULL, q.x, k), qy = __shfl_sync(FULL, q.y, k),
+                            qz = __shfl_sync(FULL, q.z, k);
+                const uint32_t qi = (uint32_t)__shfl_sync(FULL, __float_as_int(q.w), k);
+                const float dx = qx - t.x, dy = qy - t.y, dz = qz - t.z;
+                const float r2 = dx * dx + dy * dy + dz * dz + eps2f;
+                if (have && qi != ti && r2 > 0.f) acc -= rsqrtf(r2);
+            }
+            terms += cnt;
+        } else {
+            const int c = b * UT_LEAF + lane;
+            const bool ex = c < V.cnt[h - 1];
+            float4 cc = make_float4(0.f, 0.f, 0.f, 0.f), cs = cc;
+            if (ex) {
+                cc = B.c[base + V.off[h - 1] + c];
+                cs = B.s[base + V.off[h - 1] + c];
+            }
+            const float gx = cc.x - gc.x, gy = cc.y - gc.y, gz = cc.z - gc.z;
+            const bool acc_ok = ex && sqrtf(gx * gx + gy * gy + gz * gz) - gs.y > cs.z;
+            unsigned am = __ballot_sync(FULL, acc_ok);
+            while (am) {  // accepted boxes: a monopole term for every target
+                const int src = __ffs(am) - 1;
+                am &= am - 1;
+                const float bx = __shfl_sync(FULL, cc.x, src), by = __shfl_sync(FULL, cc.y, src),
+                            bz = __shfl_sync(FULL, cc.z, src), bn = __shfl_sync(FULL, cc.w, src);
+                const float dx = bx - t.x, dy = by - t.y, dz = bz - t.z;
+                if (have) acc -= bn * rsqrtf(dx * dx + dy * dy + dz * dz + eps2f);
+                terms++;
+            }
+            const unsigned om = __ballot_sync(FULL, ex && !acc_ok);
+            if (sp + __popc(om) > UT_STACK) {
+                if (lane == 0) dev_fail(st, DEV_OVERFLOW, 75, r);
+                break;
+            }
+            if (ex && !acc_ok) S[sp + __popc(om & ((1u << lane) - 1u))] = ((h - 1) << 24) | c;
+            sp += __popc(om);
+            __syncwarp();
+        }
+        if (terms >= 256) {
+            phi += (double)acc;
+            acc = 0.f;
+            terms = 0;
+        }
+    }
+    phi += (double)acc;
+    if (!have) return;
+    ub_finish(tmem[a + m], r, phi * gm, vel, stride, vbulk, halo_id, hid, n_bound, bound_own, phi_own);
 }
 
 __global__ void k_ub_fill_i8(int8_t *p, int64_t n, int8_t v)
@@ -427,13 +787,14 @@ extern "C" rs_status rs_halo_props(rs_ctx *ctx, const rs_tree *t, const rs_halos
 
 extern "C" rs_status rs_unbind(rs_ctx *ctx, const rs_tree *t, const rs_halos *hs, const int32_t *halo_id,
                                const int32_t *host, const float *pos, const float *vel, int32_t stride, int64_t n,
-                               double gm, double eps, int64_t *n_part, int64_t *n_bound, double *vbulk,
-                               int8_t *bound_own)
+                               double gm, double eps, double theta, int64_t *n_part, int64_t *n_bound,
+                               double *vbulk, int8_t *bound_own, double *phi_own)
 {
     if (!ctx) return RS_ERR_INVALID_ARG;
     if (!t || !hs || n != t->n_total || (stride != 3 && stride != 4) || !(gm >= 0) || !(eps >= 0) ||
-        (n > 0 && (!halo_id || !pos || !vel || !bound_own)))
+        !(theta >= 0 && theta < 1) || (n > 0 && (!halo_id || !pos || !vel || !bound_own)))
         return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_unbind: bad argument");
+    const int tree_on = theta > 0 ? 1 : 0;
     if (n == 0) return RS_OK;
     RS_LAUNCH(ctx, "ub_fill", k_ub_fill_i8, std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 16), 256, 0,
               bound_own, n, (int8_t)-1);
@@ -474,7 +835,7 @@ extern "C" rs_status rs_unbind(rs_ctx *ctx, const rs_tree *t, const rs_halos *hs
         RS_CUDA(ctx, cudaMemsetAsync(off, 0, sizeof(int64_t) * (H + 1), ctx->stream));
     RS_LAUNCH(ctx, "ub_bulk", k_ub_bulk, std::min<int64_t>(H, (int64_t)ctx->num_sms * 8), HP_THREADS, 0, (int)H,
               (const int64_t *)off, smem, vel, stride, vbulk);
-    RS_LAUNCH(ctx, "ub_tiles", k_ub_tiles, ceil_div(H, 256), 256, 0, (int)H, (const int64_t *)off, toff);
+    RS_LAUNCH(ctx, "ub_tiles", k_ub_tiles, ceil_div(H, 256), 256, 0, (int)H, (const int64_t *)off, tree_on, toff);
     RS_CUDA(ctx, cudaMemsetAsync(toff + H, 0, sizeof(int64_t), ctx->stream));
     RS_TRY(rs_scan_i64(ctx, toff, H + 1, nullptr));
     int64_t T = 0;
@@ -485,7 +846,63 @@ extern "C" rs_status rs_unbind(rs_ctx *ctx, const rs_tree *t, const rs_halos *hs
     if (T > 0)
         RS_LAUNCH(ctx, "ub_phi", k_ub_phi, T, UB_TILE, 0, (const int *)tm, (const int *)(tm + T),
                   (const int64_t *)off, smem, pos, vel, stride, (float)t->box, gm, (float)(eps * eps),
-                  (const double *)vbulk, halo_id, (const int *)hs->id, (unsigned long long *)n_bound, bound_own);
+                  (const double *)vbulk, halo_id, (const int *)hs->id, (unsigned long long *)n_bound, bound_own,
+                  phi_own);
+    if (tree_on && total > 0) {
+        // the sets above UB_DIRECT_MAX members: Morton order, boxes, tree walk
+        RS_WS(ctx, int64_t, tb, WS_HL_TREE, 2 * (H + 1) + 8);
+        int64_t *nbox = tb, *nleaf = tb + (H + 1);
+        RS_LAUNCH(ctx, "ub_boxcount", k_ub_boxcount, ceil_div(H, 256), 256, 0, (int)H, (const int64_t *)off,
+                  tree_on, nbox, nleaf);
+        RS_CUDA(ctx, cudaMemsetAsync(nbox + H, 0, sizeof(int64_t), ctx->stream));
+        RS_CUDA(ctx, cudaMemsetAsync(nleaf + H, 0, sizeof(int64_t), ctx->stream));
+        RS_TRY(rs_scan_i64(ctx, nbox, H + 1, nullptr));
+        RS_TRY(rs_scan_i64(ctx, nleaf, H + 1, nullptr));
+        int64_t NB = 0, NJ = 0;
+        RS_TRY(rs_read_i64(ctx, nbox + H, 1, &NB, "rs_unbind"));
+        RS_TRY(rs_read_i64(ctx, nleaf + H, 1, &NJ, "rs_unbind"));
+        if (NJ > 0) {
+            const float boxf = (float)t->box;
+            RS_WS(ctx, float4, rc, WS_HL_REF, 2 * H + 2);
+            float4 *ref = rc, *cube = rc + H;
+            RS_WS(ctx, float4, upos, WS_HL_UPOS, total);
+            RS_WS(ctx, float4, tpos, WS_HL_TPOS, total);
+            RS_WS(ctx, uint32_t, tmem, WS_HL_TMEM, total);
+            RS_WS(ctx, uint64_t, mk0, WS_HL_MK0, total);
+            RS_WS(ctx, uint64_t, mk1, WS_HL_MK1, total);
+            RS_WS(ctx, uint32_t, mv0, WS_HL_MV0, total);
+            RS_WS(ctx, uint32_t, mv1, WS_HL_MV1, total);
+            RS_LAUNCH(ctx, "ub_ref", k_ub_ref, ceil_div(H, 256), 256, 0, (int)H, (const int64_t *)off, smem, pos,
+                      stride, ref);
+            RS_LAUNCH(ctx, "ub_upos", k_ub_upos, ceil_div(total, 256), 256, 0, total, sk, smem, pos, stride,
+                      (const float4 *)ref, boxf, upos);
+            RS_LAUNCH(ctx, "ub_bbox", k_ub_bbox, std::min<int64_t>(H, (int64_t)ctx->num_sms * 4), HP_THREADS, 0,
+                      (int)H, (const int64_t *)off, tree_on, (const float4 *)upos, cube);
+            RS_LAUNCH(ctx, "ub_morton", k_ub_morton, ceil_div(total, 256), 256, 0, total, sk, (const int64_t *)off,
+                      tree_on, (const float4 *)upos, (const float4 *)cube, mk0, mv0);
+            bool malt = false;
+            RS_TRY(rs_radix_sort_u64(ctx, mk0, mk1, mv0, mv1, total, 30 + rbits, &malt));
+            RS_LAUNCH(ctx, "ub_gather", k_ub_gather, ceil_div(total, 256), 256, 0, total,
+                      (const uint32_t *)(malt ? mv1 : mv0), (const float4 *)upos, smem, tpos, tmem);
+            RS_WS(ctx, float4, bx, WS_HL_BOX, 2 * NB + 2);
+            UBoxes B;
+            B.c = bx;
+            B.s = bx + NB;
+            RS_WS(ctx, int, jb, WS_HL_JOBS, 2 * NJ + 8);
+            int *jset = jb, *jleaf = jb + NJ;
+            RS_LAUNCH(ctx, "ub_leafjobs", k_ub_leafjobs, H, 128, 0, (int)H, (const int64_t *)nleaf, jset, jleaf);
+            RS_LAUNCH(ctx, "ub_leafbox", k_ub_leafbox, ceil_div(NJ, UT_WARPS), UT_WARPS * 32, 0, NJ,
+                      (const int *)jset, (const int *)jleaf, (const int64_t *)off, (const int64_t *)nbox,
+                      (const float4 *)tpos, (float)theta, B);
+            RS_LAUNCH(ctx, "ub_upper", k_ub_upper, std::min<int64_t>(H, (int64_t)ctx->num_sms * 4), HP_THREADS, 0,
+                      (int)H, (const int64_t *)off, tree_on, (const int64_t *)nbox, (float)theta, B);
+            RS_LAUNCH(ctx, "ub_walk", k_ub_walk, ceil_div(NJ, UT_WARPS), UT_WARPS * 32, 0, NJ, (const int *)jset,
+                      (const int *)jleaf, (const int64_t *)off, (const int64_t *)nbox, (const float4 *)tpos,
+                      (const uint32_t *)tmem, B, gm, (float)(eps * eps), vel, stride, (const double *)vbulk,
+                      halo_id, (const int *)hs->id, (unsigned long long *)n_bound, bound_own, phi_own,
+                      ctx->d_status);
+        }
+    }
     RS_LAUNCH(ctx, "ub_npart", k_ub_npart, ceil_div(H, 256), 256, 0, (int)H, (const int64_t *)off, n_part);
     return rs_sync_check(ctx, "rs_unbind");
 }

@@ -74,7 +74,7 @@ def _declare(lib):
         "rs_halos_count": (i64, [P]),
         "rs_halos_export": (C.c_int, [P, P, P, P, P, P, P]),
         "rs_halo_props": (C.c_int, [P, P, P, P, i64, P, P, P, P, P]),
-        "rs_unbind": (C.c_int, [P, P, P, P, P, P, P, i32, i64, f64, f64, P, P, P, P]),
+        "rs_unbind": (C.c_int, [P, P, P, P, P, P, P, i32, i64, f64, f64, f64, P, P, P, P, P]),
         "rs_find_halos": (C.c_int, [P, P, P, i32, i64, f64, C.POINTER(rs_params), P, P, C.POINTER(rs_stats),
                                     i32]),
         "rs_profile_enable": (C.c_int, [P, i32]),
@@ -363,17 +363,19 @@ def rs_halo_props(ctx: Context, tree: Tree, halos: Halos, halo_id: torch.Tensor)
 
 
 def rs_unbind(ctx: Context, tree: Tree, halos: Halos, halo_id: torch.Tensor, host: torch.Tensor, pos: torch.Tensor,
-              vel: torch.Tensor, gm: float, eps: float = 0.0) -> dict:
-    """Sec. 3.4 / App. B single-pass unbinding: n_part, n_bound, vbulk per
-    halo and bound_own per particle (device tensors)."""
+              vel: torch.Tensor, gm: float, eps: float = 0.0, theta: float = 0.04) -> dict:
+    """Sec. 3.4 / App. B single-pass unbinding (theta = 0: direct sums; else
+    the tree for sets above 4096 members): n_part, n_bound, vbulk per halo,
+    bound_own and phi_own per particle (device tensors)."""
     H, dev, n = halos.n, pos.device, pos.shape[0]
     out = dict(n_part=torch.empty(H, dtype=torch.int64, device=dev),
                n_bound=torch.empty(H, dtype=torch.int64, device=dev),
                vbulk=torch.empty((H, 3), dtype=torch.float64, device=dev),
-               bound_own=torch.empty(n, dtype=torch.int8, device=dev))
+               bound_own=torch.empty(n, dtype=torch.int8, device=dev),
+               phi_own=torch.full((n,), float("nan"), dtype=torch.float64, device=dev))
     ctx.check(lib().rs_unbind(ctx.handle, tree.handle, halos.handle, _ptr(halo_id), _ptr(host), _ptr(pos),
-                              _ptr(vel), _stride_of(pos), n, float(gm), float(eps),
-                              *[_ptr(out[k]) for k in ("n_part", "n_bound", "vbulk", "bound_own")]))
+                              _ptr(vel), _stride_of(pos), n, float(gm), float(eps), float(theta),
+                              *[_ptr(out[k]) for k in ("n_part", "n_bound", "vbulk", "bound_own", "phi_own")]))
     return out
 
 
