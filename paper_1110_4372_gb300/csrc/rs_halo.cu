@@ -694,7 +694,8 @@ __global__ void __launch_bounds__(UT_WARPS * 32) k_ub_walk(int64_t njobs, const 
                 terms++;
             }
             const unsigned om = __ballot_sync(FULL, ex && !acc_ok);
-            if (sp + __popc(om) > UT_STACK) {
+            // stack entries hold a box index in 24 bits (sets below 2^29 members)
+            if (sp + __popc(om) > UT_STACK || __any_sync(FULL, ex && !acc_ok && c >= (1 << 24))) {
                 if (lane == 0) dev_fail(st, DEV_OVERFLOW, 75, r);
                 break;
             }
