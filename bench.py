@@ -180,6 +180,58 @@ def compare_fof(rsgpu, ctx, pos, box, dense_n, reps=3):
     return out
 
 
+def compare_per_group(rsgpu, ctx, pos, vel, box, n_sample, seed=11104372):
+    """The batched refinement (every group of a level in the same launches)
+    against the plain path of one rs_refine6d call per group, on the same
+    groups: a seeded sample of n_sample groups of the workload whose tenth
+    are its largest groups.  Each path is timed once with CUDA events on the
+    context's stream after one untimed batched call; the per-group CSR
+    slices are built before the timed region."""
+    import torch
+    p = rsgpu.params()
+    labels, _, _ = rsgpu.rs_fof3d(ctx, pos, box, p.b)
+    perm, offsets = rsgpu.rs_group_sort(ctx, labels, p.min_n)
+    off = offsets.cpu().numpy()
+    sizes = np.diff(off)
+    G = len(sizes)
+    rng = np.random.default_rng(seed)
+    k_big = min(G, max(1, n_sample // 10))
+    big = np.argsort(sizes, kind="stable")[::-1][:k_big]
+    rest = np.setdiff1d(np.arange(G), big)
+    pick = np.sort(np.concatenate([big, rng.choice(rest, min(len(rest), max(0, n_sample - k_big)),
+                                                   replace=False)]))
+    idx = np.concatenate([np.arange(off[g], off[g + 1]) for g in pick])
+    sub_perm = perm[torch.from_numpy(idx).to(perm.device)].contiguous()
+    sub_sizes = sizes[pick]
+    sub_off = np.concatenate([[0], np.cumsum(sub_sizes)]).astype(np.int64)
+    sub_off_t = torch.from_numpy(sub_off).to(perm.device)
+    one = [(sub_perm[sub_off[k]:sub_off[k + 1]],
+            torch.tensor([0, int(sub_sizes[k])], dtype=torch.int64, device=perm.device)) for k in range(len(pick))]
+    rsgpu.rs_refine6d(ctx, pos, vel, box, sub_perm, sub_off_t, p.f, p.min_n)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    tb = rsgpu.rs_refine6d(ctx, pos, vel, box, sub_perm, sub_off_t, p.f, p.min_n)
+    e1.record()
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1)
+    nodes_b = tb.info().n_nodes
+    del tb
+    nodes_p = 0
+    e0.record()
+    for pg, og in one:
+        tg = rsgpu.rs_refine6d(ctx, pos, vel, box, pg, og, p.f, p.min_n)
+        nodes_p += tg.info().n_nodes
+        del tg
+    e1.record()
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    return {"groups": int(len(pick)), "members": int(sub_off[-1]), "largest": int(sub_sizes.max()),
+            "batched_ms": batched_ms, "plain_per_group_ms": plain_ms, "speedup": plain_ms / batched_ms,
+            "nodes_batched": int(nodes_b), "nodes_plain": int(nodes_p),
+            "sample": f"{len(pick)} of {G} groups (seed {seed}): the {k_big} largest and the rest at random"}
+
+
 def reference_arm(args, cat, cfg_json):
     """The oracle, as it stands, on host cores: each step one bounded sample."""
     side = args.ref_side
@@ -252,6 +304,8 @@ def main():
     ap.add_argument("--nn-seed", type=int, default=11104372, help="seed of those subsets")
     ap.add_argument("--fof-accel", type=int, default=None, metavar="DENSE_N",
                     help="also time the plain 3D FOF against the accelerated variant (Sec. 3.1) alone")
+    ap.add_argument("--per-group", type=int, default=None, metavar="GROUPS",
+                    help="also time the batched refinement against one rs_refine6d call per group on a sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-side", type=float, default=1.0 / 6.0, help="sub-cube side for the CPU baseline")
@@ -377,6 +431,9 @@ def main():
     fof_cmp = None
     if args.fof_accel is not None:
         fof_cmp = compare_fof(rsgpu, ctx, pos, cat.box, args.fof_accel)
+    per_group = None
+    if args.per_group is not None:
+        per_group = compare_per_group(rsgpu, ctx, pos, vel, cat.box, args.per_group)
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -403,6 +460,8 @@ def main():
     }
     if fof_cmp is not None:
         line["fof3d_compare"] = fof_cmp
+    if per_group is not None:
+        line["refine_per_group_compare"] = per_group
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
