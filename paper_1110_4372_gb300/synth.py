@@ -228,6 +228,92 @@ def generate(name: str = "c1", *, seed: int | None = None, n: int | None = None,
                      comp_n=comp_n)
 
 
+# Independent 6D groups for the batching stress workload: sizes log-uniform
+# on [nmin, nmax]; each group an NFW host with 0-max_subs co-spatial subhalos
+# (same centre, each 1-10% of the host's particles, bulk velocity offset by
+# U[1, 3] sigma_host in an isotropic direction).  Radii and dispersions use
+# the density of the benchmark boxes (32^3 particles per 10 Mpc/h cube).
+GROUP_CONFIGS = {
+    "c4": dict(n_groups=200_000, nmin=20, nmax=500_000, max_subs=12),
+    "c4s": dict(n_groups=2_000, nmin=20, nmax=20_000, max_subs=12),  # small case of the same recipe
+}
+GROUP_NBAR = 32768 / 10.0 ** 3
+GROUP_BOX = 1000.0
+
+
+@dataclasses.dataclass
+class GroupCatalogue:
+    pos: np.ndarray          # (N, 3) float32 in [0, box), groups back to back
+    vel: np.ndarray          # (N, 3) float32, km/s
+    box: float
+    offsets: np.ndarray      # (n_groups + 1,) int64: group g is rows offsets[g]:offsets[g+1]
+    truth: np.ndarray        # (N,) int32: 0 for the host, k for the group's k-th subhalo
+
+    @property
+    def n(self) -> int:
+        return int(self.pos.shape[0])
+
+
+def _group(g, cfg, seed, cs, table):
+    """One group from its own substream (so groups can be drawn in any chunks)."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, g])))
+    n = int(np.exp(rng.uniform(np.log(cfg["nmin"]), np.log(cfg["nmax"] + 1.0))))
+    n = min(max(n, cfg["nmin"]), cfg["nmax"])
+    k = int(rng.integers(0, cfg["max_subs"] + 1))
+    sub_n = np.floor(rng.uniform(0.01, 0.10, size=k) * n).astype(np.int64)
+    sub_n = sub_n[sub_n >= 10]
+    host_n = n - int(sub_n.sum())
+    counts = np.concatenate([[host_n], sub_n]).astype(np.int64)
+    masses = np.concatenate([[n], sub_n]).astype(np.float64)
+    centre = rng.random(3) * GROUP_BOX
+    sig_host = _sigma1d(n)
+    bulk = np.zeros((len(counts), 3))
+    bulk[0] = rng.standard_normal(3) * 300.0
+    if len(sub_n):
+        dv = _isotropic(rng, len(sub_n)) * (rng.uniform(1.0, 3.0, size=len(sub_n)) * sig_host)[:, None]
+        bulk[1:] = bulk[0] + dv
+    R = _virial_radius(masses, GROUP_NBAR)
+    sig = _sigma1d(masses)
+    lev = rng.integers(0, N_C_LEVELS, size=len(counts))
+    ids = np.repeat(np.arange(len(counts)), counts)
+    m = ids.shape[0]
+    sq = np.sqrt(rng.random(m)) * N_U_GRID
+    i0 = np.minimum(sq.astype(np.int64), N_U_GRID - 1)
+    w = sq - i0
+    L = lev[ids]
+    x = table[L, i0] * (1.0 - w) + table[L, i0 + 1] * w
+    r = R[ids] * x / cs[L]
+    p = centre + _isotropic(rng, m) * r[:, None]
+    v = bulk[ids] + rng.standard_normal((m, 3)) * sig[ids][:, None]
+    perm = rng.permutation(m)
+    return p[perm], v[perm], ids[perm].astype(np.int32)
+
+
+def groups(name: str = "c4s", *, first: int = 0, count: int | None = None,
+           seed: int | None = None) -> GroupCatalogue:
+    """Groups first .. first+count-1 of the independent-group workload
+    ``name`` (all of them by default); any slice equals the same rows of the
+    whole draw, so the workload can be streamed in chunks of whole groups."""
+    cfg = GROUP_CONFIGS[name]
+    if seed is None:
+        seed = BASE_SEED + 4
+    if count is None:
+        count = cfg["n_groups"] - first
+    cs, table = _inverse_cdf_table()
+    L = float(np.float32(GROUP_BOX))
+    parts = [_group(g, cfg, seed, cs, table) for g in range(first, first + count)]
+    sizes = np.array([len(q[0]) for q in parts], np.int64)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    if count == 0:
+        e = np.zeros((0, 3), np.float32)
+        return GroupCatalogue(pos=e, vel=e.copy(), box=L, offsets=offsets, truth=np.zeros(0, np.int32))
+    pos = _wrap32(np.concatenate([q[0] for q in parts]), L)
+    vel = np.concatenate([q[1] for q in parts]).astype(np.float32)
+    truth = np.concatenate([q[2] for q in parts])
+    return GroupCatalogue(pos=np.ascontiguousarray(pos), vel=np.ascontiguousarray(vel), box=L, offsets=offsets,
+                          truth=truth)
+
+
 def uniform(n: int, box: float, seed: int, vel_sigma: float = 20.0) -> Catalogue:
     """Plain uniform box (no halos), for edge cases and small tests."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -22,3 +22,41 @@ def test_halo_counts_follow_config():
     assert 0 < len(subs) <= 8 * 2500  # 1-8 per host, minus those under 10 particles
     assert c.comp_n[subs].min() >= 10
     assert (c.truth >= 0).sum() == c.comp_n.sum()
+
+
+def test_independent_groups_recipe_and_chunks():
+    """The batching-stress groups: sizes log-uniform in range, 0-12
+    co-spatial subhalos moving at 1-3 sigma_host, and any chunk of groups
+    equal to the same rows of the whole draw."""
+    whole = synth.groups("c4s", count=300)
+    sizes = np.diff(whole.offsets)
+    assert sizes.min() >= 20 and sizes.max() <= 20_000
+    # log-uniform: about half the groups below the geometric midpoint
+    mid = np.sqrt(20 * 20_000)
+    assert 0.4 < np.mean(sizes < mid) < 0.6
+    assert whole.pos.min() >= 0 and whole.pos.max() < whole.box
+    part = synth.groups("c4s", first=100, count=50)
+    a, b = whole.offsets[100], whole.offsets[150]
+    assert np.array_equal(part.pos, whole.pos[a:b]) and np.array_equal(part.vel, whole.vel[a:b])
+    assert np.array_equal(part.offsets, whole.offsets[100:151] - a)
+    n_subs = [len(np.unique(whole.truth[whole.offsets[g]:whole.offsets[g + 1]])) - 1 for g in range(300)]
+    assert min(n_subs) >= 0 and max(n_subs) <= 12 and np.mean(n_subs) > 2
+    # a subhalo shares the host's centre; its bulk velocity is offset by 1-3 sigma_host
+    checked = 0
+    for g in range(300):
+        s0, s1 = whole.offsets[g], whole.offsets[g + 1]
+        t = whole.truth[s0:s1]
+        if t.max() == 0 or sizes[g] < 5000:
+            continue
+        p, v = whole.pos[s0:s1].astype(np.float64), whole.vel[s0:s1].astype(np.float64)
+        host_c = np.median(p[t == 0], axis=0)
+        sig = 300.0 * (sizes[g] / 4000.0) ** (1 / 3)
+        for k in np.unique(t[t > 0]):
+            sel = t == k
+            if sel.sum() < 200:
+                continue
+            assert np.linalg.norm(np.median(p[sel], axis=0) - host_c) < 0.5 * np.abs(p[t == 0] - host_c).max()
+            dv = np.linalg.norm(v[sel].mean(0) - v[t == 0].mean(0)) / sig
+            assert 0.7 < dv < 3.3
+            checked += 1
+    assert checked >= 3
