@@ -28,8 +28,8 @@
 // the tree for the 32 targets of a leaf, accepting a box only when the whole
 // leaf lies beyond d(theta).  Periodic differences take the far-side
 // coordinate minus the box first (exact for x >= box/2).
+#include <algorithm>
 #include <cmath>
-#include <new>
 
 #include "rs_refine.cuh"
 
@@ -718,15 +718,6 @@ __global__ void k_ub_fill_i8(int8_t *p, int64_t n, int8_t v)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
-}
-
-template <typename T>
-T *carve_h(char *&p, int64_t count)
-{
-    T *r = (T *)p;
-    size_t b = sizeof(T) * (size_t)(count > 0 ? count : 1);
-    p += (b + 255) / 256 * 256;
-    return r;
 }
 
 // ids sorted with their ranks, in the workspace
