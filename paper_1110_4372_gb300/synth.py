@@ -53,6 +53,7 @@ class Catalogue:
     truth: np.ndarray      # (N,) int32 generating component id, -1 = background
     comp_parent: np.ndarray  # (n_comp,) int32 parent component, -1 for hosts
     comp_n: np.ndarray     # (n_comp,) int64 particles drawn for each component
+    comp_center: np.ndarray | None = None  # (n_comp, 3) float64 generating centre (not wrapped)
 
     @property
     def n(self) -> int:
@@ -225,7 +226,7 @@ def generate(name: str = "c1", *, seed: int | None = None, n: int | None = None,
     truth = truth[perm]
     return Catalogue(pos=np.ascontiguousarray(pos), vel=np.ascontiguousarray(vel), box=L,
                      truth=truth, comp_parent=comp_parent.astype(np.int32),
-                     comp_n=comp_n)
+                     comp_n=comp_n, comp_center=comp_center)
 
 
 # Independent 6D groups for the batching stress workload: sizes log-uniform
