@@ -302,6 +302,13 @@ def rs_assign(ctx: Context, tree: Tree, pos: torch.Tensor, vel: torch.Tensor, bo
     return halo_id, nh.value
 
 
+def particle_gm(nbar: float, omega_m: float = 0.27) -> float:
+    """G times the particle mass in (km/s)^2 Mpc/h for particles sampling the
+    matter density Omega_m rho_crit at nbar per (Mpc/h)^3 (G = 4.30091e-9
+    Mpc (km/s)^2 / Msun, rho_crit = 2.77536627e11 h^2 Msun / Mpc^3)."""
+    return 4.30091e-9 * omega_m * 2.77536627e11 / nbar
+
+
 class Halos:
     """Library-owned per-halo table from :func:`rs_assign_ex`."""
 
