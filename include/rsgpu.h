@@ -86,6 +86,14 @@ rs_status rs_set_stream(rs_ctx *ctx, void *cuda_stream);
 const char *rs_status_string(rs_status s);
 const char *rs_last_error(const rs_ctx *ctx);
 
+/* Failure-detection self-test.  One device thread waits, at most limit polls
+ * (1 <= limit <= 2^24, about 0.1 us each), for a flag that only it can set,
+ * and sets it first when set_flag is nonzero.  A wait that runs out is
+ * recorded in the device status word like every bounded wait of the library,
+ * and this synchronising call returns RS_ERR_TIMEOUT; the status word is then
+ * clear and the context usable.  With set_flag the call returns RS_OK. */
+rs_status rs_selftest_wait(rs_ctx *ctx, int32_t set_flag, int64_t limit);
+
 /* Sec. 3.1: the linking length b times the cube root of the mean volume per
  * particle, l = b * cbrt(box^3 / n), in float64.  0 for n = 0. */
 double rs_linking_length(int64_t n, double box, double b);

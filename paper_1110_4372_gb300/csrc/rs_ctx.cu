@@ -18,6 +18,36 @@ extern "C" void rs_params_default(rs_params *p)
     p->nn_seed = 0;
 }
 
+namespace {
+
+// One thread waits, at most `limit` polls, for a flag that it sets itself
+// only when `set` is nonzero; running out records a timeout in the status
+// word, as every bounded wait of the library does.
+__global__ void k_wait_flag(int *flag, int set, int64_t limit, rs_dev_status *st)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (set) atomicExch(flag, 1);
+    volatile int *f = flag;
+    for (int64_t i = 0; i < limit; i++) {
+        if (*f) return;
+        __nanosleep(64);
+    }
+    dev_fail(st, DEV_TIMEOUT, 90, limit);
+}
+
+}  // namespace
+
+extern "C" rs_status rs_selftest_wait(rs_ctx *ctx, int32_t set_flag, int64_t limit)
+{
+    if (!ctx) return RS_ERR_INVALID_ARG;
+    if (limit < 1 || limit > ((int64_t)1 << 24))
+        return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_selftest_wait: limit must be in [1, 2^24]");
+    RS_WS(ctx, int, flag, WS_SELFTEST, 4);
+    RS_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+    RS_LAUNCH(ctx, "selftest_wait", k_wait_flag, 1, 32, 0, flag, (int)(set_flag != 0), limit, ctx->d_status);
+    return rs_sync_check(ctx, "rs_selftest_wait");
+}
+
 extern "C" double rs_linking_length(int64_t n, double box, double b)
 {
     if (n <= 0) return 0.0;

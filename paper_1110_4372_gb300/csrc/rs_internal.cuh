@@ -58,6 +58,7 @@ enum rs_ws_slot {
     WS_HL_TMEM, WS_HL_MK0, WS_HL_MK1, WS_HL_MV0, WS_HL_MV1, WS_HL_BOX, WS_HL_JOBS,
     WS_AS_0, WS_AS_1, WS_AS_2, WS_AS_3, WS_AS_4, WS_AS_5, WS_AS_6, WS_AS_7, WS_AS_8, WS_AS_9,
     WS_IO_POS, WS_IO_VEL, WS_IO_LAB, WS_IO_HID, WS_IO_PERM, WS_IO_OFF,
+    WS_SELFTEST,
     WS_NUM_SLOTS
 };
 

@@ -55,6 +55,7 @@ def _declare(lib):
         "rs_status_string": (C.c_char_p, [C.c_int]),
         "rs_last_error": (C.c_char_p, [P]),
         "rs_linking_length": (f64, [i64, f64, f64]),
+        "rs_selftest_wait": (C.c_int, [P, i32, i64]),
         "rs_fof3d": (C.c_int, [P, P, i32, i64, f64, f64, P, P, P]),
         "rs_fof3d_accel": (C.c_int, [P, P, i32, i64, f64, f64, i32, P, P, P]),
         "rs_group_sort": (C.c_int, [P, P, i64, i32, P, P, i64, C.POINTER(i64), C.POINTER(i64)]),
@@ -157,6 +158,13 @@ def params(**kw) -> rs_params:
     for k, v in kw.items():
         setattr(p, k, v)
     return p
+
+
+def rs_selftest_wait(ctx: Context, set_flag: bool, limit: int = 20000) -> None:
+    """Failure-detection self-test: a bounded device wait on a flag nothing
+    sets (set_flag False) raises RsError with RS_ERR_TIMEOUT; the context
+    stays usable."""
+    ctx.check(lib().rs_selftest_wait(ctx.handle, 1 if set_flag else 0, int(limit)))
 
 
 def rs_linking_length(n: int, box: float, b: float = 0.28) -> float:
