@@ -180,6 +180,19 @@ def compare_fof(rsgpu, ctx, pos, box, dense_n, reps=3):
     return out
 
 
+def sample_groups(sizes, n_sample: int, seed: int):
+    """A seeded sample of group indices, ascending: the largest tenth of
+    n_sample groups (by size) and the rest drawn at random without
+    replacement.  Returns (indices, number taken by size)."""
+    G = len(sizes)
+    rng = np.random.default_rng(seed)
+    k_big = min(G, max(1, n_sample // 10))
+    big = np.argsort(sizes, kind="stable")[::-1][:k_big]
+    rest = np.setdiff1d(np.arange(G), big)
+    extra = rng.choice(rest, min(len(rest), max(0, n_sample - k_big)), replace=False)
+    return np.sort(np.concatenate([big, extra]).astype(np.int64)), k_big
+
+
 def compare_per_group(rsgpu, ctx, pos, vel, box, n_sample, seed=11104372):
     """The batched refinement (every group of a level in the same launches)
     against the plain path of one rs_refine6d call per group, on the same
@@ -194,12 +207,7 @@ def compare_per_group(rsgpu, ctx, pos, vel, box, n_sample, seed=11104372):
     off = offsets.cpu().numpy()
     sizes = np.diff(off)
     G = len(sizes)
-    rng = np.random.default_rng(seed)
-    k_big = min(G, max(1, n_sample // 10))
-    big = np.argsort(sizes, kind="stable")[::-1][:k_big]
-    rest = np.setdiff1d(np.arange(G), big)
-    pick = np.sort(np.concatenate([big, rng.choice(rest, min(len(rest), max(0, n_sample - k_big)),
-                                                   replace=False)]))
+    pick, k_big = sample_groups(sizes, n_sample, seed)
     idx = np.concatenate([np.arange(off[g], off[g + 1]) for g in pick])
     sub_perm = perm[torch.from_numpy(idx).to(perm.device)].contiguous()
     sub_sizes = sizes[pick]

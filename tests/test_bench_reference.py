@@ -28,3 +28,21 @@ def test_reference_arm_json_line():
     per_step = float(d["cpu_baseline"]["sample"].split("(")[1].split(" ")[0])
     assert abs(per_step / (d["ms_per_step"] * 1e-3) - d["value"]) <= 1e-6 * d["value"]
     assert "workload" in d["config"]
+
+
+def test_per_group_sample_selection():
+    """The per-group comparison's sample: seeded, ascending, distinct, the
+    largest tenth included, and all groups when the sample asks for more."""
+    import importlib.util
+    import numpy as np
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    sizes = np.random.default_rng(3).integers(10, 100000, 5000)
+    a, k = bench.sample_groups(sizes, 200, 7)
+    b, _ = bench.sample_groups(sizes, 200, 7)
+    assert np.array_equal(a, b) and len(a) == 200 and k == 20
+    assert np.all(np.diff(a) > 0)
+    assert set(np.argsort(sizes)[::-1][:20]) <= set(a.tolist())
+    c, _ = bench.sample_groups(sizes, 10000, 7)
+    assert np.array_equal(c, np.arange(5000))

@@ -150,3 +150,18 @@ def test_across_the_periodic_boundary():
     pos = synth.wrap(pos, box)
     lab, _, nc = oracle.fof3d_accel(pos, box, l=l)
     assert nc == 1 and lab[-1] == 0
+
+
+def test_empty_single_and_threshold_zero():
+    lab, _, nc = oracle.fof3d_accel(np.zeros((0, 3), np.float32), 10.0, l=1.0)
+    assert len(lab) == 0 and nc == 0
+    lab, _, nc = oracle.fof3d_accel(np.array([[1, 2, 3]], np.float32), 10.0, l=1.0)
+    assert list(lab) == [0] and nc == 0
+    # with dense_n = 0 any particle with a neighbour is dense: particle 0 (one
+    # neighbour at 0.5) joins particle 2, 1.2 away across the face, at 2l = 1.2
+    p = np.array([[1.0, 1, 1], [1.5, 1, 1], [9.75, 1, 1]], np.float32)
+    lab, _, nc = oracle.fof3d_accel(p, 10.0, l=0.65, dense_n=0)
+    assert list(lab) == [0, 0, 0] and nc == 1
+    assert np.array_equal(lab, closed_form(p, 10.0, 0.65, 0)[0])
+    plain, _, _ = oracle.fof3d(p, 10.0, l=0.65)
+    assert list(plain) == [0, 0, 2]
