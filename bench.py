@@ -193,13 +193,17 @@ def sample_groups(sizes, n_sample: int, seed: int):
     return np.sort(np.concatenate([big, extra]).astype(np.int64)), k_big
 
 
-def compare_per_group(rsgpu, ctx, pos, vel, box, n_sample, seed=11104372):
+def compare_per_group(rsgpu, ctx, pos, vel, box, n_sample, seed=11104372, reps=3):
     """The batched refinement (every group of a level in the same launches)
     against the plain path of one rs_refine6d call per group, on the same
     groups: a seeded sample of n_sample groups of the workload whose tenth
-    are its largest groups.  Each path is timed once with CUDA events on the
-    context's stream after one untimed batched call; the per-group CSR
-    slices are built before the timed region."""
+    are its largest groups.  After one untimed call of each, every path is
+    timed reps times with CUDA events on the context's stream and the median
+    is reported.  The per-group CSR slices are built before the timed region;
+    the plain path's time includes the host synchronisation that each
+    rs_refine6d call makes (it returns host scalars), which is part of
+    launching one call per group.  Both paths must produce the same node
+    count, or no speedup is reported."""
     import torch
     p = rsgpu.params()
     labels, _, _ = rsgpu.rs_fof3d(ctx, pos, box, p.b)
@@ -215,29 +219,84 @@ def compare_per_group(rsgpu, ctx, pos, vel, box, n_sample, seed=11104372):
     sub_off_t = torch.from_numpy(sub_off).to(perm.device)
     one = [(sub_perm[sub_off[k]:sub_off[k + 1]],
             torch.tensor([0, int(sub_sizes[k])], dtype=torch.int64, device=perm.device)) for k in range(len(pick))]
-    rsgpu.rs_refine6d(ctx, pos, vel, box, sub_perm, sub_off_t, p.f, p.min_n)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    tb = rsgpu.rs_refine6d(ctx, pos, vel, box, sub_perm, sub_off_t, p.f, p.min_n)
-    e1.record()
-    torch.cuda.synchronize()
-    batched_ms = e0.elapsed_time(e1)
-    nodes_b = tb.info().n_nodes
-    del tb
-    nodes_p = 0
-    e0.record()
-    for pg, og in one:
-        tg = rsgpu.rs_refine6d(ctx, pos, vel, box, pg, og, p.f, p.min_n)
-        nodes_p += tg.info().n_nodes
-        del tg
-    e1.record()
-    torch.cuda.synchronize()
-    plain_ms = e0.elapsed_time(e1)
+
+    def batched():
+        t = rsgpu.rs_refine6d(ctx, pos, vel, box, sub_perm, sub_off_t, p.f, p.min_n)
+        n_nodes = t.info().n_nodes
+        t.free()
+        return n_nodes
+
+    def plain():
+        n_nodes = 0
+        for pg, og in one:
+            t = rsgpu.rs_refine6d(ctx, pos, vel, box, pg, og, p.f, p.min_n)
+            n_nodes += t.info().n_nodes
+            t.free()
+        return n_nodes
+
+    out = {}
+    for name, call in (("batched", batched), ("plain", plain)):
+        call()
+        torch.cuda.synchronize()
+        times, nodes = [], None
+        for _ in range(max(1, reps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            nodes = call()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        out[name] = (statistics.median(times), times, nodes)
+    (b_ms, b_all, nodes_b), (p_ms, p_all, nodes_p) = out["batched"], out["plain"]
+    same = nodes_b == nodes_p
     return {"groups": int(len(pick)), "members": int(sub_off[-1]), "largest": int(sub_sizes.max()),
-            "batched_ms": batched_ms, "plain_per_group_ms": plain_ms, "speedup": plain_ms / batched_ms,
-            "nodes_batched": int(nodes_b), "nodes_plain": int(nodes_p),
+            "batched_ms": b_ms, "plain_per_group_ms": p_ms, "speedup": (p_ms / b_ms) if same else None,
+            "batched_ms_all": [round(t, 2) for t in b_all], "plain_ms_all": [round(t, 2) for t in p_all],
+            "nodes_batched": int(nodes_b), "nodes_plain": int(nodes_p), "same_nodes": bool(same), "reps": reps,
+            "plain_includes": "one host synchronisation per rs_refine6d call",
             "sample": f"{len(pick)} of {G} groups (seed {seed}): the {k_big} largest and the rest at random"}
+
+
+def time_halo_props(rsgpu, ctx, pos, vel, box, thetas=(0.04, 0.0)):
+    """Sec. 3.3-3.5.1 and App. B after the hot path: rs_assign_ex (the halo
+    table), rs_halo_props (centres, hosts) and rs_unbind at each theta,
+    each timed once with CUDA events on the context's stream after one
+    untimed call of the whole sequence."""
+    import torch
+    p = rsgpu.params()
+    n = pos.shape[0]
+    labels, _, _ = rsgpu.rs_fof3d(ctx, pos, box, p.b)
+    perm, offsets = rsgpu.rs_group_sort(ctx, labels, p.min_n)
+    tree = rsgpu.rs_refine6d(ctx, pos, vel, box, perm, offsets, p.f, p.min_n)
+    gm = rsgpu.particle_gm(n / box ** 3)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    out = {"gm": gm}
+    for it in range(2):
+        (hid, halos), t_as = timed(lambda: rsgpu.rs_assign_ex(ctx, tree, pos, vel, box, p))
+        hp, t_hp = timed(lambda: rsgpu.rs_halo_props(ctx, tree, halos, hid))
+        ub_t = {}
+        for th in thetas:
+            if it == 0 and th == 0.0:
+                continue  # the direct sum is timed once
+            ub, t_ub = timed(lambda: rsgpu.rs_unbind(ctx, tree, halos, hid, hp["host"], pos, vel, gm, 0.0, th))
+            ub_t[th] = (t_ub, ub)
+    npart = {th: int(u.get("n_part").sum()) for th, (_, u) in ub_t.items()}
+    nbound = {th: int(u.get("n_bound").sum()) for th, (_, u) in ub_t.items()}
+    sq = {th: float((u.get("n_part").double() ** 2).sum()) for th, (_, u) in ub_t.items()}
+    out.update({"halos": halos.n, "assign_ex_ms": t_as, "halo_props_ms": t_hp,
+                "unbind": {f"theta={th:g}": {"ms": t, "set_members": npart[th], "bound": nbound[th],
+                                              "sum_set_size_sq": sq[th]} for th, (t, _) in ub_t.items()}})
+    tree.free()
+    return out
 
 
 def reference_arm(args, cat, cfg_json):
@@ -310,10 +369,14 @@ def main():
     ap.add_argument("--nn-subset", type=int, default=0,
                     help="nodes above this size take l from a random subset of this size (Sec. 3.2; 0: exact)")
     ap.add_argument("--nn-seed", type=int, default=11104372, help="seed of those subsets")
-    ap.add_argument("--fof-accel", type=int, default=None, metavar="DENSE_N",
-                    help="also time the plain 3D FOF against the accelerated variant (Sec. 3.1) alone")
-    ap.add_argument("--per-group", type=int, default=None, metavar="GROUPS",
-                    help="also time the batched refinement against one rs_refine6d call per group on a sample")
+    ap.add_argument("--fof-accel", type=int, default=16, metavar="DENSE_N",
+                    help="also time the plain 3D FOF against the accelerated variant (Sec. 3.1) alone "
+                         "(negative: skip)")
+    ap.add_argument("--per-group", type=int, default=2000, metavar="GROUPS",
+                    help="also time the batched refinement against one rs_refine6d call per group on a sample "
+                         "of this many groups (0: skip)")
+    ap.add_argument("--halo-props", action="store_true",
+                    help="also time rs_assign_ex, rs_halo_props and rs_unbind (tree and direct sum)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-side", type=float, default=1.0 / 6.0, help="sub-cube side for the CPU baseline")
@@ -437,11 +500,23 @@ def main():
     path_frac = b_alg / (ms * 1e-3) / 1e9 / peak
 
     fof_cmp = None
-    if args.fof_accel is not None:
+    if args.fof_accel >= 0:
+        s = ClockSampler(local)
+        s.start()
         fof_cmp = compare_fof(rsgpu, ctx, pos, cat.box, args.fof_accel)
+        fof_cmp["clocks"] = s.stop()
     per_group = None
-    if args.per_group is not None:
+    if args.per_group > 0:
+        s = ClockSampler(local)
+        s.start()
         per_group = compare_per_group(rsgpu, ctx, pos, vel, cat.box, args.per_group)
+        per_group["clocks"] = s.stop()
+    halo_props = None
+    if args.halo_props:
+        s = ClockSampler(local)
+        s.start()
+        halo_props = time_halo_props(rsgpu, ctx, pos, vel, cat.box)
+        halo_props["clocks"] = s.stop()
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -470,6 +545,8 @@ def main():
         line["fof3d_compare"] = fof_cmp
     if per_group is not None:
         line["refine_per_group_compare"] = per_group
+    if halo_props is not None:
+        line["halo_props_timing"] = halo_props
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
