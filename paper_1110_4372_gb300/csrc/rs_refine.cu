@@ -445,8 +445,9 @@ __global__ void __launch_bounds__(NT, MINB)
                         if (!act || c <= q) continue;
                         const float d2 = d2_32(pq, vq, pc, vc, met);
                         if (d2 > part) continue;
-                        bool link = d2 <= lo;
-                        if (!link && (d2 <= hi || (d2 >= tlo && d2 <= thi))) {
+                        // below both bands: a friend, and not a tie-band pair
+                        bool link = d2 < fminf(lo, tlo);
+                        if (!link) {
                             const double e = d2_64(pq, vq, pc, vc, met);
                             link = e <= l2;
                             if (l2 > 0 && e != l2 && fabs(sqrt(e) - l) <= 1e-6 * l) tie++;
@@ -709,8 +710,9 @@ __global__ void __launch_bounds__(TINY_WARPS * 32)
                 if (!act || c <= lane || dc > part) continue;
                 const float d2 = d2_32(p, v, pc, vc, met);
                 if (d2 > part) continue;
-                bool link = d2 <= lo;
-                if (!link && (d2 <= hi || (d2 >= tlo && d2 <= thi))) {
+                // below both bands: a friend, and not a tie-band pair
+                bool link = d2 < fminf(lo, tlo);
+                if (!link) {
                     const double e = d2_64(p, v, pc, vc, met);
                     link = e <= l2;
                     if (l2 > 0 && e != l2 && fabs(sqrt(e) - l) <= 1e-6 * l) tie++;
@@ -1428,15 +1430,14 @@ __device__ __forceinline__ int pair_test(const LinkLim &lm, const Metric6 &met, 
 {
     const float d2 = d2_32(pa, va, pb, vb, met);
     if (d2 > lm.part) return 0;
-    if (d2 <= lm.lo) return 1;
-    if (d2 <= lm.hi || (d2 >= lm.tlo && d2 <= lm.thi)) {
-        const Metric6 m = *met64;
-        const double l2 = *l2p, l = sqrt(l2);
-        const double e64 = d2_64(pa, va, pb, vb, m);
-        const int tie = (l2 > 0 && e64 != l2 && fabs(sqrt(e64) - l) <= 1e-6 * l) ? 2 : 0;
-        return (e64 <= l2 ? 1 : 0) | tie;
-    }
-    return 0;
+    // below both bands (the linking band and the wider tie band): a friend,
+    // and not a tie-band pair
+    if (d2 < fminf(lm.lo, lm.tlo)) return 1;
+    const Metric6 m = *met64;
+    const double l2 = *l2p, l = sqrt(l2);
+    const double e64 = d2_64(pa, va, pb, vb, m);
+    const int tie = (l2 > 0 && e64 != l2 && fabs(sqrt(e64) - l) <= 1e-6 * l) ? 2 : 0;
+    return (e64 <= l2 ? 1 : 0) | tie;
 }
 
 // Join a and b; returns the smaller of the two roots it joined (a member of

@@ -5,10 +5,12 @@ benchmark times), on sampled outputs the oracle can compute one by one:
   oracle's breadth-first search over the whole box, equals the CUDA label
   set (both directions: every oracle member has the label, and the group has
   no other member);
-* hierarchy and assignment: sampled groups (up to 60k members) are refined
-  and assigned by the oracle from its own member lists; node sets per
-  (level, smallest member) and halo ids must match, with sigma, centre and
-  linking length within 1e-6 relative.
+* hierarchy and assignment: sampled groups -- a spread of sizes up to 60k
+  members plus the largest group of at most LARGE_MAX members (a few hundred
+  thousand, the multi-level big-node path) -- are refined and assigned by
+  the oracle from its own member lists; node sets per (level, smallest
+  member), child and tie-band counts and every halo id must match exactly,
+  with sigma, centre and linking length within 1e-6 relative.
 """
 import numpy as np
 import pytest
@@ -25,6 +27,7 @@ torch = pytest.importorskip("torch")
 N_PARTICLES = 24        # random particles whose 3D group is checked
 N_GROUPS = 12           # sampled groups refined and assigned by the oracle
 MAX_GROUP = 60000
+LARGE_MIN, LARGE_MAX = 200_000, 450_000
 
 
 @pytest.fixture(scope="module")
@@ -84,27 +87,46 @@ def test_fof_groups_of_sampled_particles(full):
         assert lab == comp.min()
 
 
+def _check_group(full, g):
+    cat, labels, grid = full["cat"], full["labels"], full["grid"]
+    nbar = cat.n / cat.box ** 3
+    members = grid.component(int(g))  # the oracle's own member list
+    assert len(members) == np.count_nonzero(labels == labels[g])
+    t = oracle.refine(cat.pos, cat.vel, cat.box, members.astype(np.int32), np.array([0, len(members)]))
+    hid_o, _ = oracle.assign(t, cat.n, cat.box, 360.0, nbar)
+    gd = _gpu_nodes_of(full, members)
+    od = oracle_tree_dict(t)
+    matched, _ = compare_trees(gd, od, cat.box)
+    assert np.array_equal(full["hid"][members], hid_o[members]), f"group {g}: halo ids differ"
+    n_nodes = t.n_nodes
+    t.free()
+    return matched, n_nodes
+
+
 def test_hierarchy_and_assignment_of_sampled_groups(full):
     rng = np.random.default_rng(11104373)
-    cat, labels, grid = full["cat"], full["labels"], full["grid"]
+    labels = full["labels"]
     sizes = np.bincount(labels)
     candidates = np.flatnonzero((sizes >= 10) & (sizes <= MAX_GROUP))
     # spread the sample over group sizes: a third from the largest eligible
     by_size = candidates[np.argsort(sizes[candidates])]
     pick = list(rng.choice(by_size[: len(by_size) * 2 // 3], N_GROUPS - N_GROUPS // 3, replace=False))
     pick += list(by_size[-(N_GROUPS // 3):])
-    nbar = cat.n / cat.box ** 3
     checked = 0
     for g in pick:
-        members = grid.component(int(g))  # the oracle's own member list
-        assert len(members) == sizes[g]
-        t = oracle.refine(cat.pos, cat.vel, cat.box, members.astype(np.int32), np.array([0, len(members)]))
-        hid_o, _ = oracle.assign(t, cat.n, cat.box, 360.0, nbar)
-        gd = _gpu_nodes_of(full, members)
-        od = oracle_tree_dict(t)
-        matched, excused = compare_trees(gd, od, cat.box)
-        if excused == 0:
-            assert np.array_equal(full["hid"][members], hid_o[members]), f"group {g}: halo ids differ"
+        matched, n_nodes = _check_group(full, g)
+        assert matched == n_nodes
         checked += matched
-        t.free()
     assert checked > N_GROUPS
+
+
+def test_hierarchy_of_a_large_group(full):
+    """The largest group of at most LARGE_MAX members (at least LARGE_MIN):
+    several big-node levels (k-d order, sampled bracket, box hierarchy)
+    before the subtree kernels take over."""
+    sizes = np.bincount(full["labels"])
+    ok = np.flatnonzero((sizes >= LARGE_MIN) & (sizes <= LARGE_MAX))
+    assert len(ok), "the 134M workload has a group in the size range"
+    g = int(ok[np.argmax(sizes[ok])])
+    matched, n_nodes = _check_group(full, g)
+    assert matched == n_nodes > 20
