@@ -15,6 +15,7 @@ samples of the same workload (sub-cubes of the box), on rank 0 only.
 from __future__ import annotations
 
 import argparse
+import collections
 import json
 import math
 import os
@@ -131,6 +132,19 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), or the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
 
 
 def sub_cube(cat, frac_side: float):
@@ -299,6 +313,177 @@ def time_halo_props(rsgpu, ctx, pos, vel, box, thetas=(0.04, 0.0)):
     return out
 
 
+# ---- batching stress: independent groups streamed in chunks ----
+def plan_chunks(sizes, chunk_particles, task_particles=20_000_000):
+    """Chunks of whole consecutive groups with at most chunk_particles
+    particles each (a larger group makes a chunk of its own), and inside
+    every chunk the drawing tasks of about task_particles particles.
+    Returns (chunks [(first, end)], tasks [(first, end)], chunk of each task)."""
+    G = len(sizes)
+    chunks, a, acc = [], 0, 0
+    for g in range(G):
+        if acc and acc + sizes[g] > chunk_particles:
+            chunks.append((a, g))
+            a, acc = g, 0
+        acc += int(sizes[g])
+    if G:
+        chunks.append((a, G))
+    tasks, task_chunk = [], []
+    for k, (a, b) in enumerate(chunks):
+        t0, acc = a, 0
+        for g in range(a, b):
+            acc += int(sizes[g])
+            if acc >= task_particles or g == b - 1:
+                tasks.append((t0, g + 1))
+                task_chunk.append(k)
+                t0, acc = g + 1, 0
+    return chunks, tasks, task_chunk
+
+
+def _draw_groups_to_shm(task):
+    """Worker: draws groups first .. first+count-1 of the workload into a
+    shared-memory block (pos then vel, float32) and returns its name."""
+    from multiprocessing import shared_memory
+    name, first, count = task
+    g = synth.groups(name, first=first, count=count)
+    shm = shared_memory.SharedMemory(create=True, size=max(1, 24 * g.n))
+    buf = np.ndarray((2, g.n, 3), np.float32, buffer=shm.buf)
+    buf[0] = g.pos
+    buf[1] = g.vel
+    shm.close()
+    return shm.name, g.n
+
+
+def stream_groups(args, rsgpu, ctx):
+    """The batching-stress workload: every group of the independent-group
+    recipe, drawn on the host cores (a spawn pool writing into shared memory)
+    and refined on the GPU in chunks of whole groups, one rs_refine6d call
+    per chunk with the chunk's group offsets (no 3D FOF).  Each chunk's host
+    to device copy and refinement are timed with CUDA events; the per-group
+    comparison runs on a seeded sample of the first chunk's groups."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    import torch
+    name = args.config
+    cfg = synth.GROUP_CONFIGS[name]
+    G = min(args.groups or cfg["n_groups"], cfg["n_groups"])
+    sizes = synth.group_sizes(name, first=0, count=G)
+    chunks, spans, task_chunk = plan_chunks(sizes, args.chunk_particles)
+    tasks = [(name, a, b - a) for a, b in spans]
+    cap = int(max(sizes[a:b].sum() for a, b in chunks))
+    dpos = torch.empty((cap, 3), dtype=torch.float32, device="cuda")
+    dvel = torch.empty((cap, 3), dtype=torch.float32, device="cuda")
+    hbuf = torch.empty((2, cap, 3), dtype=torch.float32, pin_memory=True)
+    perm = torch.arange(cap, dtype=torch.int32, device="cuda")
+    p = rsgpu.params()
+    box = float(np.float32(synth.GROUP_BOX))
+    workers = max(1, (os.cpu_count() or 2) - 1)
+    refine_ms = copy_ms = 0.0
+    n_nodes = n_levels = 0
+    per_group = None
+    done_particles = 0
+    t_wall = time.perf_counter()
+    ctx_mp = mp.get_context("spawn")
+    with ctx_mp.Pool(workers) as pool:
+        # at most two tasks per worker in flight, so the shared memory the
+        # workers fill ahead of the GPU stays bounded
+        pending = collections.deque()
+        nxt = 0
+        ti = 0
+        for k, (a, b) in enumerate(chunks):
+            m = 0
+            while ti < len(tasks) and task_chunk[ti] == k:
+                while nxt < len(tasks) and len(pending) < 2 * workers:
+                    pending.append(pool.apply_async(_draw_groups_to_shm, (tasks[nxt],)))
+                    nxt += 1
+                shm_name, nt = pending.popleft().get()
+                shm = shared_memory.SharedMemory(name=shm_name)
+                src = np.ndarray((2, nt, 3), np.float32, buffer=shm.buf)
+                hbuf[0, m:m + nt].numpy()[:] = src[0]
+                hbuf[1, m:m + nt].numpy()[:] = src[1]
+                del src
+                shm.close()
+                shm.unlink()
+                m += nt
+                ti += 1
+            off = torch.from_numpy(np.concatenate([[0], np.cumsum(sizes[a:b])]).astype(np.int64)).cuda()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            dpos[:m].copy_(hbuf[0, :m], non_blocking=True)
+            dvel[:m].copy_(hbuf[1, :m], non_blocking=True)
+            e1.record()
+            tree = rsgpu.rs_refine6d(ctx, dpos[:m], dvel[:m], box, perm[:m], off, p.f, p.min_n)
+            e2.record()
+            torch.cuda.synchronize()
+            info = tree.info()
+            tree.free()
+            copy_ms += e0.elapsed_time(e1)
+            refine_ms += e1.elapsed_time(e2)
+            n_nodes += info.n_nodes
+            n_levels = max(n_levels, info.n_levels)
+            done_particles += m
+            if k == 0 and args.per_group > 0:
+                per_group = compare_groups_sample(rsgpu, ctx, dpos[:m], dvel[:m], box, sizes[a:b], args.per_group)
+    wall = time.perf_counter() - t_wall
+    return {"groups": G, "particles": done_particles, "chunks": len(chunks), "chunk_particles_max": cap,
+            "refine_ms": refine_ms, "copy_ms": copy_ms, "wall_s": wall, "n_nodes": n_nodes, "n_levels": n_levels,
+            "generation": f"{workers} spawn workers drawing groups into shared memory, overlapped with the GPU",
+            "per_group": per_group}
+
+
+def compare_groups_sample(rsgpu, ctx, pos, vel, box, sizes, n_sample, seed=11104376, reps=3):
+    """One rs_refine6d call over a seeded sample of groups (given by their
+    sizes, back to back in pos/vel) against one call per group on the same
+    groups; medians of reps CUDA-event timings, node counts must agree."""
+    import torch
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    pick, k_big = sample_groups(sizes, n_sample, seed)
+    idx = np.concatenate([np.arange(off[g], off[g + 1]) for g in pick]).astype(np.int32)
+    sub_perm = torch.from_numpy(idx).cuda()
+    sub_sizes = sizes[pick]
+    sub_off = np.concatenate([[0], np.cumsum(sub_sizes)]).astype(np.int64)
+    sub_off_t = torch.from_numpy(sub_off).cuda()
+    one = [(sub_perm[sub_off[j]:sub_off[j + 1]],
+            torch.tensor([0, int(sub_sizes[j])], dtype=torch.int64, device="cuda")) for j in range(len(pick))]
+    p = rsgpu.params()
+
+    def batched():
+        t = rsgpu.rs_refine6d(ctx, pos, vel, box, sub_perm, sub_off_t, p.f, p.min_n)
+        nn = t.info().n_nodes
+        t.free()
+        return nn
+
+    def plain():
+        nn = 0
+        for pg, og in one:
+            t = rsgpu.rs_refine6d(ctx, pos, vel, box, pg, og, p.f, p.min_n)
+            nn += t.info().n_nodes
+            t.free()
+        return nn
+
+    res = {}
+    for label, call in (("batched", batched), ("plain", plain)):
+        call()
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            nn = call()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        res[label] = (statistics.median(times), nn)
+    same = res["batched"][1] == res["plain"][1]
+    return {"groups": int(len(pick)), "members": int(sub_off[-1]), "largest": int(sub_sizes.max()),
+            "batched_ms": res["batched"][0], "plain_per_group_ms": res["plain"][0],
+            "speedup": res["plain"][0] / res["batched"][0] if same else None, "same_nodes": bool(same),
+            "nodes": int(res["batched"][1]), "reps": reps,
+            "plain_includes": "one host synchronisation per rs_refine6d call",
+            "sample": f"{len(pick)} of {len(sizes)} groups of the first chunk (seed {seed}): the {k_big} largest "
+                      f"and the rest at random"}
+
+
 def reference_arm(args, cat, cfg_json):
     """The oracle, as it stands, on host cores: each step one bounded sample."""
     side = args.ref_side
@@ -315,6 +500,7 @@ def reference_arm(args, cat, cfg_json):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": cfg_json,
             "cpu_baseline": {"value": v, "unit": "particles/s", "cores": 1, "kind": "oracle",
+                             "host_cores": os.cpu_count(), "cpu_model": cpu_model(),
                              "sample": f"particles in the sub-cube [0, {side:g} L)^3 of the workload "
                                        f"({tot_p // max(args.steps, 1)} per step): 3D FOF + refinement + "
                                        f"assignment, float64 C oracle, single thread"},
@@ -359,12 +545,50 @@ def whole_job_rate(units_per_rank: int, world: int, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
+STRESS_METRIC = "particles/s through 6D refinement of independent co-spatial groups streamed in chunks"
+
+
+def stress_main(args, world, rank, local):
+    """--config c4 / c4s: the batching-stress workload streamed through
+    rs_refine6d (one process; replicas run the same stream)."""
+    import torch
+    from paper_1110_4372_gb300 import rsgpu
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the batching-stress workload has no oracle "
+                              "timing leg; its parity is tested on its small case"}))
+        return
+    torch.cuda.set_device(local)
+    dist = init_replicas(world, local)
+    ctx = rsgpu.Context()
+    sampler = ClockSampler(local)
+    sampler.start()
+    r = stream_groups(args, rsgpu, ctx)
+    clocks = sampler.stop()
+    if rank != 0:
+        return
+    cfg = synth.GROUP_CONFIGS[args.config]
+    v = r["particles"] / (r["refine_ms"] * 1e-3)
+    e = r["particles"] / ((r["refine_ms"] + r["copy_ms"]) * 1e-3)
+    line = {"metric": STRESS_METRIC, "value": v, "unit": "particles/s", "n_gpus": world, "steps": 1, "warmup": 0,
+            "ms_per_step": r["refine_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{r['groups']} independent groups of log-uniform size in [{cfg['nmin']}, "
+                                   f"{cfg['nmax']}], NFW hosts with 0-{cfg['max_subs']} co-spatial subhalos "
+                                   f"offset by 1-3 sigma in velocity", "name": args.config,
+                       "f": 0.7, "min_n": 10, "chunk_particles": args.chunk_particles},
+            "e2e": {"value": e, "unit": "particles/s", "h2d_bytes_per_step": 24 * r["particles"],
+                    "d2h_bytes_per_step": 0, "note": "host-to-device copy of every chunk plus its refinement"},
+            "clocks": clocks, "stream": r}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default="c3", choices=sorted(WORKLOADS) + sorted(synth.GROUP_CONFIGS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nn-subset", type=int, default=0,
                     help="nodes above this size take l from a random subset of this size (Sec. 3.2; 0: exact)")
@@ -377,6 +601,10 @@ def main():
                          "of this many groups (0: skip)")
     ap.add_argument("--halo-props", action="store_true",
                     help="also time rs_assign_ex, rs_halo_props and rs_unbind (tree and direct sum)")
+    ap.add_argument("--groups", type=int, default=None,
+                    help="batching-stress workloads (c4, c4s): refine only the first this many groups")
+    ap.add_argument("--chunk-particles", type=float, default=1.0e9,
+                    help="batching-stress workloads: particles per streamed chunk (whole groups)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-side", type=float, default=1.0 / 6.0, help="sub-cube side for the CPU baseline")
@@ -384,6 +612,8 @@ def main():
     args = ap.parse_args()
 
     world, rank, local = replica_env()
+    if args.config in synth.GROUP_CONFIGS:
+        return stress_main(args, world, rank, local)
 
     cfg = synth.CONFIGS[args.config]
     cfg_json = {"workload": WORKLOADS[args.config], "name": args.config, "particles": cfg["n"], "box": cfg["box"],
@@ -445,7 +675,32 @@ def main():
     ms = max_over_ranks(ms, dist)
     value = whole_job_rate(n, world, ms * 1e-3)
 
+    workspace_bytes = rsgpu.rs_workspace_bytes(ctx)
+
+    # ---- the comparisons (rank 0), on the resident inputs ----
+    fof_cmp = per_group = halo_props = None
+    if rank == 0:
+        if args.fof_accel >= 0:
+            s = ClockSampler(local)
+            s.start()
+            fof_cmp = compare_fof(rsgpu, ctx, pos, cat.box, args.fof_accel)
+            fof_cmp["clocks"] = s.stop()
+        if args.per_group > 0:
+            s = ClockSampler(local)
+            s.start()
+            per_group = compare_per_group(rsgpu, ctx, pos, vel, cat.box, args.per_group)
+            per_group["clocks"] = s.stop()
+        if args.halo_props:
+            s = ClockSampler(local)
+            s.start()
+            halo_props = time_halo_props(rsgpu, ctx, pos, vel, cat.box)
+            halo_props["clocks"] = s.stop()
+
     # ---- end to end through the C ABI with pinned host buffers ----
+    # (the device-resident inputs are released first: this leg has its own
+    # device copies inside the library's workspace)
+    del pos, vel, halo
+    torch.cuda.empty_cache()
     e2e = None
     if not args.no_e2e:
         hp = torch.from_numpy(cat.pos).pin_memory()
@@ -499,29 +754,11 @@ def main():
     b_alg = BYTES_FOF_PER_PARTICLE * n + BYTES_LEVEL_PER_MEMBER * stats["sum_level_members"]
     path_frac = b_alg / (ms * 1e-3) / 1e9 / peak
 
-    fof_cmp = None
-    if args.fof_accel >= 0:
-        s = ClockSampler(local)
-        s.start()
-        fof_cmp = compare_fof(rsgpu, ctx, pos, cat.box, args.fof_accel)
-        fof_cmp["clocks"] = s.stop()
-    per_group = None
-    if args.per_group > 0:
-        s = ClockSampler(local)
-        s.start()
-        per_group = compare_per_group(rsgpu, ctx, pos, vel, cat.box, args.per_group)
-        per_group["clocks"] = s.stop()
-    halo_props = None
-    if args.halo_props:
-        s = ClockSampler(local)
-        s.start()
-        halo_props = time_halo_props(rsgpu, ctx, pos, vel, cat.box)
-        halo_props["clocks"] = s.stop()
-
     cpu = None
     if not args.no_cpu_baseline:
         npart, t = time_oracle_sample(cat, args.cpu_side, args.nn_subset, args.nn_seed)
         cpu = {"value": npart / t, "unit": "particles/s", "cores": 1, "kind": "oracle",
+               "host_cores": os.cpu_count(), "cpu_model": cpu_model(),
                "sample": f"{npart} particles in the sub-cube [0, {args.cpu_side:.4g} L)^3 of the workload: "
                          f"3D FOF + refinement + assignment, float64 C oracle, single thread, {t:.1f} s"}
 
@@ -539,7 +776,7 @@ def main():
         "stage_ms": {k: round(v, 3) for k, v in sorted(stages.items(), key=lambda kv: -kv[1])},
         "top_kernels_ms": {k: round(v[1] / args.steps, 3) for k, v in
                            sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]},
-        "stats": stats,
+        "stats": stats, "workspace_gb": round(workspace_bytes / 1e9, 2),
     }
     if fof_cmp is not None:
         line["fof3d_compare"] = fof_cmp

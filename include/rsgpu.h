@@ -86,6 +86,46 @@ rs_status rs_set_stream(rs_ctx *ctx, void *cuda_stream);
 const char *rs_status_string(rs_status s);
 const char *rs_last_error(const rs_ctx *ctx);
 
+/* Launch choices per size class, picked by measurement.  None of them
+ * changes a result: every setting computes the same partitions, linking
+ * lengths and halo ids (only which CTA or warp does which work, and in
+ * which order).  A context starts with rs_tuning_default's values, which
+ * are the ones the library's tuner chose on a GB300 (the tuner, its
+ * coordinate descent and its result check are in the Python package).
+ *   link_blocks_per_sm  big-node link search: resident 256-thread blocks per
+ *                       SM the kernel is compiled for (4, 5 or 6);
+ *   nn_blocks_per_sm    big-node nearest-neighbour search (5, 6 or 7);
+ *   kd_levels           big-node levels whose members are put in k-d order
+ *                       (0-3; deeper levels keep their parent's order);
+ *   bracket_min         big nodes above this many members search with the
+ *                       sampled bracket of the linking length (>= 1024);
+ *   mid_max             subtrees of at most this many members run in the
+ *                       128-thread tier (33-256); larger ones up to 1024 run
+ *                       in the 256-thread tier;
+ *   tiny_max            subtrees of at most this many members run one per
+ *                       warp (10-32);
+ *   small_ctas_per_sm, mid_ctas_per_sm, tiny_ctas_per_sm
+ *                       persistent CTAs per SM of the three subtree tiers
+ *                       (1-2, 1-8, 1-16);
+ *   fof_link_ctas_per_sm  CTAs per SM of the grid-stride 3D link (1-64). */
+typedef struct {
+    int32_t link_blocks_per_sm;
+    int32_t nn_blocks_per_sm;
+    int32_t kd_levels;
+    int32_t bracket_min;
+    int32_t mid_max;
+    int32_t tiny_max;
+    int32_t small_ctas_per_sm;
+    int32_t mid_ctas_per_sm;
+    int32_t tiny_ctas_per_sm;
+    int32_t fof_link_ctas_per_sm;
+} rs_tuning;
+
+void rs_tuning_default(rs_tuning *t);
+/* RS_ERR_INVALID_ARG (and no change) if a field is outside its range. */
+rs_status rs_set_tuning(rs_ctx *ctx, const rs_tuning *t);
+rs_status rs_get_tuning(const rs_ctx *ctx, rs_tuning *t);
+
 /* Failure-detection self-test.  One device thread waits, at most limit polls
  * (1 <= limit <= 2^24, about 0.1 us each), for a flag that only it can set,
  * and sets it first when set_flag is nonzero.  A wait that runs out is
@@ -161,10 +201,12 @@ rs_status rs_group_sort(rs_ctx *ctx, const int32_t *labels, int64_t n, int32_t m
  * only; there is no context for a message).
  *
  * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture on the device.  All calls share the one array
- * and it keeps the last call's contents: calls that overlap on the GPU (from
- * different streams or host threads) race on it and give wrong results. */
+ * (cudaGetSymbolAddress) with that device current.  Every call synchronises
+ * cuda_stream before it returns (it reads the device status word), so no
+ * call can be made while that stream is being captured into a CUDA graph.
+ * All calls share the one array and it keeps the last call's contents: calls
+ * that overlap on the GPU (from different streams or host threads) race on
+ * it and give wrong results. */
 rs_status rs_fof3d_static(const float *pos, int32_t stride, int64_t n, double box, double b, int32_t *labels,
                           void *cuda_stream);
 
@@ -322,8 +364,11 @@ typedef struct {
  * 0, pos, vel, fof_labels and halo_id are device pointers; with
  * host_buffers = 1 they are host pointers (pinned memory gives full copy
  * speed): the inputs are copied to the context's workspace and both outputs
- * copied back before the call returns.  fof_labels and stats may be NULL.
- * Synchronises. */
+ * copied back before the call returns.  The copies overlap the kernels: the
+ * positions go first, the velocities travel on a second stream of the
+ * context while the 3D FOF and the group sort run, and fof_labels comes back
+ * on it while the refinement runs; the caller's buffers must stay valid
+ * until the call returns.  fof_labels and stats may be NULL.  Synchronises. */
 rs_status rs_find_halos(rs_ctx *ctx, const float *pos, const float *vel, int32_t stride, int64_t n, double box,
                         const rs_params *params, int32_t *fof_labels, int32_t *halo_id, rs_stats *stats,
                         int32_t host_buffers);
@@ -341,6 +386,11 @@ rs_status rs_profile_read(rs_ctx *ctx, int32_t i, const char **name, int64_t *la
 /* Number of kernel launches issued on the context since the last reset
  * (counted whether or not profiling is enabled). */
 int64_t rs_launch_count(const rs_ctx *ctx);
+/* Bytes of device workspace the context holds now.  The workspace grows to
+ * the largest call seen; when the device runs out of memory, the scratch of
+ * the 3D FOF and of the group sort is released while neither runs, and the
+ * allocation is retried (the 1.07B-particle path relies on this). */
+int64_t rs_workspace_bytes(const rs_ctx *ctx);
 
 #ifdef __cplusplus
 }

@@ -1,24 +1,52 @@
 // rs_api.cu -- the whole path behind one call (rs_find_halos).
 #include "rs_refine.cuh"
 
-extern "C" rs_status rs_find_halos(rs_ctx *ctx, const float *pos, const float *vel, int32_t stride, int64_t n,
-                                   double box, const rs_params *params, int32_t *fof_labels, int32_t *halo_id,
-                                   rs_stats *stats, int32_t host_buffers)
+// The context's second stream and its three events, created on first use.
+static rs_status rs_io_streams(rs_ctx *ctx)
 {
-    if (!ctx) return RS_ERR_INVALID_ARG;
-    if (!params || n < 0 || (stride != 3 && stride != 4) || (n > 0 && (!pos || !vel || !halo_id)))
-        return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_find_halos: bad argument");
-    if (n >= ((int64_t)1 << 31)) return rs_fail(ctx, RS_ERR_TOO_LARGE, "rs_find_halos: n >= 2^31");
-    if (stats) *stats = rs_stats{};
-    if (n == 0) return RS_OK;
+    if (!ctx->aux) RS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+    for (auto &e : ctx->ev_io)
+        if (!e) RS_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return RS_OK;
+}
+
+// On every return of a host-buffer call: nothing of it may still run on the
+// second stream (its copies read caller buffers and the workspace).
+static rs_status rs_io_drain(rs_ctx *ctx, rs_status s)
+{
+    if (ctx->aux) {
+        cudaError_t e = cudaStreamSynchronize(ctx->aux);
+        if (e != cudaSuccess && s == RS_OK) return rs_cuda_fail(ctx, e, "rs_find_halos: second stream");
+    }
+    return s;
+}
+
+static rs_status find_halos(rs_ctx *ctx, const float *pos, const float *vel, int32_t stride, int64_t n, double box,
+                            const rs_params *params, int32_t *fof_labels, int32_t *halo_id, rs_stats *stats,
+                            int32_t host_buffers)
+{
     const float *dpos = pos, *dvel = vel;
     const size_t in_bytes = sizeof(float) * (size_t)stride * (size_t)n;
+    // With host buffers the copies overlap the kernels: positions go first on
+    // the context's stream (the 3D FOF needs them), velocities on a second
+    // stream while the 3D FOF and the group sort run, and the 3D labels (when
+    // asked for) come back on it while the refinement runs.
+    cudaEvent_t ev_vel = nullptr, ev_lab = nullptr, ev_lab_done = nullptr;
     if (host_buffers) {
         float *p = (float *)rs_ws(ctx, WS_IO_POS, in_bytes);
         float *v = (float *)rs_ws(ctx, WS_IO_VEL, in_bytes);
-        if (!p || !v) return RS_ERR_OOM;
+        if (!p || !v) return ctx->fixed_ws ? RS_ERR_INTERNAL : RS_ERR_OOM;
+        RS_TRY(rs_io_streams(ctx));
+        ev_vel = ctx->ev_io[0];
+        ev_lab = ctx->ev_io[1];
+        ev_lab_done = ctx->ev_io[2];
         RS_CUDA(ctx, cudaMemcpyAsync(p, pos, in_bytes, cudaMemcpyHostToDevice, ctx->stream));
-        RS_CUDA(ctx, cudaMemcpyAsync(v, vel, in_bytes, cudaMemcpyHostToDevice, ctx->stream));
+        // the second stream starts after everything already on the context's
+        // stream (nothing may still read the velocity workspace)
+        RS_CUDA(ctx, cudaEventRecord(ev_lab, ctx->stream));
+        RS_CUDA(ctx, cudaStreamWaitEvent(ctx->aux, ev_lab, 0));
+        RS_CUDA(ctx, cudaMemcpyAsync(v, vel, in_bytes, cudaMemcpyHostToDevice, ctx->aux));
+        RS_CUDA(ctx, cudaEventRecord(ev_vel, ctx->aux));
         dpos = p;
         dvel = v;
     }
@@ -32,8 +60,22 @@ extern "C" rs_status rs_find_halos(rs_ctx *ctx, const float *pos, const float *v
         if (!hid) return RS_ERR_OOM;
     }
     RS_TRY(rs_fof3d(ctx, dpos, stride, n, box, params->b, labels, nullptr, nullptr));
+    const size_t ob = sizeof(int32_t) * (size_t)n;
+    if (host_buffers && fof_labels) {
+        RS_CUDA(ctx, cudaEventRecord(ev_lab, ctx->stream));
+        RS_CUDA(ctx, cudaStreamWaitEvent(ctx->aux, ev_lab, 0));
+        RS_CUDA(ctx, cudaMemcpyAsync(fof_labels, labels, ob, cudaMemcpyDeviceToHost, ctx->aux));
+        RS_CUDA(ctx, cudaEventRecord(ev_lab_done, ctx->aux));
+    }
     int64_t G = 0, M = 0;
     RS_TRY(rs_group_sort(ctx, labels, n, params->min_n, perm, offsets, ocap, &G, &M));
+    if (G > 0 && rs_fault("offsets")) {
+        // injected fault: a decreasing boundary, which the refinement's
+        // argument check must turn into RS_ERR_INVALID_ARG
+        static const int64_t bad = -1;
+        RS_CUDA(ctx, cudaMemcpy(offsets + 1, &bad, sizeof(int64_t), cudaMemcpyHostToDevice));
+    }
+    if (host_buffers) RS_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ev_vel, 0));
     rs_tree *tree = nullptr;
     RS_TRY(rs_refine6d_sampled(ctx, dpos, dvel, stride, n, box, perm, offsets, G, params->f, params->min_n,
                                params->nn_subset, params->nn_seed, &tree));
@@ -52,11 +94,9 @@ extern "C" rs_status rs_find_halos(rs_ctx *ctx, const float *pos, const float *v
             stats->sum_big_level_members = tree->sum_big_level_members;
             stats->n_fallback_levels = tree->n_fallback_levels;
         }
-        const size_t ob = sizeof(int32_t) * (size_t)n;
         if (host_buffers) {
             cudaError_t e = cudaMemcpyAsync(halo_id, hid, ob, cudaMemcpyDeviceToHost, ctx->stream);
-            if (e == cudaSuccess && fof_labels)
-                e = cudaMemcpyAsync(fof_labels, labels, ob, cudaMemcpyDeviceToHost, ctx->stream);
+            if (e == cudaSuccess && fof_labels) e = cudaStreamWaitEvent(ctx->stream, ev_lab_done, 0);
             if (e != cudaSuccess) s = rs_cuda_fail(ctx, e, "rs_find_halos: copy out");
         } else if (fof_labels) {
             cudaError_t e = cudaMemcpyAsync(fof_labels, labels, ob, cudaMemcpyDeviceToDevice, ctx->stream);
@@ -66,4 +106,18 @@ extern "C" rs_status rs_find_halos(rs_ctx *ctx, const float *pos, const float *v
     }
     rs_tree_free(tree);
     return s;
+}
+
+extern "C" rs_status rs_find_halos(rs_ctx *ctx, const float *pos, const float *vel, int32_t stride, int64_t n,
+                                   double box, const rs_params *params, int32_t *fof_labels, int32_t *halo_id,
+                                   rs_stats *stats, int32_t host_buffers)
+{
+    if (!ctx) return RS_ERR_INVALID_ARG;
+    if (!params || n < 0 || (stride != 3 && stride != 4) || (n > 0 && (!pos || !vel || !halo_id)))
+        return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_find_halos: bad argument");
+    if (n >= ((int64_t)1 << 31)) return rs_fail(ctx, RS_ERR_TOO_LARGE, "rs_find_halos: n >= 2^31");
+    if (stats) *stats = rs_stats{};
+    if (n == 0) return RS_OK;
+    const rs_status s = find_halos(ctx, pos, vel, stride, n, box, params, fof_labels, halo_id, stats, host_buffers);
+    return host_buffers ? rs_io_drain(ctx, s) : s;
 }

@@ -1,6 +1,8 @@
 // rs_ctx.cu -- context, workspace, status reporting and launch accounting.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "rs_internal.cuh"
@@ -81,6 +83,41 @@ rs_status rs_cuda_fail(rs_ctx *ctx, cudaError_t e, const char *where)
     return rs_fail(ctx, e == cudaErrorMemoryAllocation ? RS_ERR_OOM : RS_ERR_CUDA, m);
 }
 
+extern "C" void rs_tuning_default(rs_tuning *t)
+{
+    if (!t) return;
+    t->link_blocks_per_sm = 5;
+    t->nn_blocks_per_sm = 6;
+    t->kd_levels = 2;
+    t->bracket_min = 4096;
+    t->mid_max = 256;
+    t->tiny_max = 32;
+    t->small_ctas_per_sm = 2;
+    t->mid_ctas_per_sm = 8;
+    t->tiny_ctas_per_sm = 8;
+    t->fof_link_ctas_per_sm = 32;
+}
+
+extern "C" rs_status rs_set_tuning(rs_ctx *c, const rs_tuning *t)
+{
+    if (!c || !t) return RS_ERR_INVALID_ARG;
+    auto in = [](int32_t v, int32_t lo, int32_t hi) { return v >= lo && v <= hi; };
+    if (!in(t->link_blocks_per_sm, 4, 6) || !in(t->nn_blocks_per_sm, 5, 7) || !in(t->kd_levels, 0, 3) ||
+        !in(t->bracket_min, 1024, 1 << 30) || !in(t->mid_max, 33, 256) || !in(t->tiny_max, 10, 32) ||
+        !in(t->small_ctas_per_sm, 1, 2) || !in(t->mid_ctas_per_sm, 1, 8) || !in(t->tiny_ctas_per_sm, 1, 16) ||
+        !in(t->fof_link_ctas_per_sm, 1, 64))
+        return rs_fail(c, RS_ERR_INVALID_ARG, "rs_set_tuning: a field is outside its range");
+    c->tune = *t;
+    return RS_OK;
+}
+
+extern "C" rs_status rs_get_tuning(const rs_ctx *c, rs_tuning *t)
+{
+    if (!c || !t) return RS_ERR_INVALID_ARG;
+    *t = c->tune;
+    return RS_OK;
+}
+
 extern "C" rs_status rs_create(rs_ctx **out, void *cuda_stream)
 {
     if (!out) return RS_ERR_INVALID_ARG;
@@ -117,6 +154,12 @@ extern "C" void rs_destroy(rs_ctx *c)
         cudaEventDestroy(r.b);
     }
     for (auto e : c->ev_free) cudaEventDestroy(e);
+    for (auto e : c->ev_io)
+        if (e) cudaEventDestroy(e);
+    if (c->aux) {
+        cudaStreamSynchronize(c->aux);
+        cudaStreamDestroy(c->aux);
+    }
     delete c;
 }
 
@@ -133,18 +176,75 @@ extern "C" const char *rs_last_error(const rs_ctx *c)
     return c->last_error.c_str();
 }
 
+bool rs_fault(const char *site)
+{
+    const char *v = getenv("RS_FAULT");
+    if (!v || !*v) return false;
+    const size_t k = strlen(site);
+    for (const char *p = v; *p;) {
+        const char *e = strchr(p, ',');
+        const size_t len = e ? (size_t)(e - p) : strlen(p);
+        if (len == k && strncmp(p, site, k) == 0) return true;
+        if (!e) break;
+        p = e + 1;
+    }
+    return false;
+}
+
+// Frees the 3D FOF and group-sort slots whose call is not running (their
+// contents are scratch of that call); true if anything was freed.
+static bool release_idle_slots(rs_ctx *c, int keep)
+{
+    bool freed = false;
+    for (int s = 0; s < WS_NUM_SLOTS; s++) {
+        const bool fof = s >= WS_FOF_CELLKEY && s <= WS_FOF_ACC;
+        const bool gs = s == WS_GS_COUNT || s == WS_GS_FLAG;
+        if (s == keep || !c->ws_ptr[s] || !((fof && !c->in_fof) || (gs && !c->in_gs))) continue;
+        if (!freed) {
+            cudaStreamSynchronize(c->stream);
+            if (c->aux) cudaStreamSynchronize(c->aux);
+        }
+        cudaFree(c->ws_ptr[s]);
+        c->ws_ptr[s] = nullptr;
+        c->ws_size[s] = 0;
+        freed = true;
+    }
+    return freed;
+}
+
+size_t rs_ws_total(const rs_ctx *c)
+{
+    size_t t = 0;
+    for (int s = 0; s < WS_NUM_SLOTS; s++) t += c->ws_size[s];
+    return t;
+}
+
 void *rs_ws(rs_ctx *c, int slot, size_t bytes)
 {
     if (c->ws_size[slot] >= bytes) return c->ws_ptr[slot];
+    if (c->fixed_ws) {
+        c->last_error = "fixed workspace slot " + std::to_string(slot) + " holds " +
+                        std::to_string(c->ws_size[slot]) + " bytes, " + std::to_string(bytes) + " needed";
+        return nullptr;
+    }
+    if (rs_fault("alloc")) {
+        c->last_error = "workspace allocation of " + std::to_string(bytes) + " bytes failed (injected: RS_FAULT=alloc)";
+        return nullptr;
+    }
     if (c->ws_ptr[slot]) {
         cudaStreamSynchronize(c->stream);
         cudaFree(c->ws_ptr[slot]);
         c->ws_ptr[slot] = nullptr;
         c->ws_size[slot] = 0;
     }
-    size_t want = bytes + bytes / 8 + 256;  // a little headroom against regrowth
+    // a little headroom against regrowth (at most 64 MB)
+    size_t want = bytes + std::min<size_t>(bytes / 8, (size_t)64 << 20) + 256;
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, want);
+    if (e == cudaErrorMemoryAllocation && release_idle_slots(c, slot)) {
+        cudaGetLastError();
+        e = cudaMalloc(&p, want);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         c->last_error = "workspace allocation of " + std::to_string(want) + " bytes failed";
@@ -239,6 +339,8 @@ extern "C" rs_status rs_profile_read(rs_ctx *c, int32_t i, const char **name, in
 }
 
 extern "C" int64_t rs_launch_count(const rs_ctx *c) { return c ? c->launches : 0; }
+
+extern "C" int64_t rs_workspace_bytes(const rs_ctx *c) { return c ? (int64_t)rs_ws_total(c) : 0; }
 
 rs_status rs_sync_check(rs_ctx *c, const char *where)
 {

@@ -325,14 +325,16 @@ __global__ void __launch_bounds__(FOF_THREADS, 6) k_fof_link(const uint32_t *n_c
     }
 }
 
+// (find_limit bounds each find; it is RS_SPIN_LIMIT except under the
+// injected fault RS_FAULT=timeout1, where it is 1)
 __global__ void k_fof_rootmin(const uint32_t *n_cells_p, const uint32_t *cell_start, const uint32_t *idx,
-                              int *parent, int *root_min, rs_dev_status *st)
+                              int *parent, int *root_min, int find_limit, rs_dev_status *st)
 {
     const int64_t M = *n_cells_p;
     for (int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; A < M; A += (int64_t)gridDim.x * blockDim.x) {
         uint32_t m = 0xffffffffu;
         for (uint32_t q = cell_start[A]; q < cell_start[A + 1]; q++) m = min(m, idx[q]);
-        int r = uf_find(parent, (int)A, st);
+        int r = uf_find_n(parent, (int)A, st, find_limit);
         atomicMin(&root_min[r], (int)m);
     }
 }
@@ -581,15 +583,11 @@ __global__ void __launch_bounds__(FOF_THREADS) k_acc_join(int64_t n, const uint3
 
 rs_status fof_geometry(rs_ctx *ctx, int64_t n, double box, double b, FofGeom *g)
 {
-    double l = rs_linking_length(n, box, b);
-    if (!(l > 0)) return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_fof3d: linking length must be positive");
     // fine side s with sqrt(3) s (1 + 2 err) < l, err = float32 error of the
     // fine-cell coordinate in cell units (2.0001 u Gf)
-    const double u = 5.9604644775390625e-08;
-    double gf_est = box * std::sqrt(3.0) / l + 16.0;
-    double err = 2.0001 * u * gf_est * 1.01;
-    double s_max = l * (1.0 - 1e-7) / (std::sqrt(3.0) * (1.0 + 2.0 * err));
-    double gc = std::ceil(box / (4.0 * s_max));
+    const FofGridSize gs = fof_grid_size(n, box, b);
+    const double l = gs.l, gf_est = gs.gf_est, err = gs.err, gc = gs.gc;
+    if (!(l > 0)) return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_fof3d: linking length must be positive");
     if (gc < 3) return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_fof3d: box narrower than about seven linking lengths");
     if (gc * gc * gc >= 4294967295.0) return rs_fail(ctx, RS_ERR_TOO_LARGE, "rs_fof3d: more than 2^32 coarse cells");
     g->Gc = (int32_t)gc;
@@ -642,6 +640,7 @@ rs_status fof_run(rs_ctx *ctx, const float *pos, int32_t stride, int64_t n, doub
         if (n_centres) *n_centres = 0;
         return RS_OK;
     }
+    RsStageGuard running(&ctx->in_fof);
     FofGeom g;
     RS_TRY(fof_geometry(ctx, n, box, b, &g));
     const int64_t T = FOF_THREADS;
@@ -677,7 +676,7 @@ rs_status fof_run(rs_ctx *ctx, const float *pos, int32_t stride, int64_t n, doub
               (const uint32_t *)flag, cell_of, cell_start, cell_key, table, (const uint32_t *)n_cells);
     RS_WS(ctx, uint64_t, occ, WS_FOF_OCC, n);
     RS_CUDA(ctx, cudaMemsetAsync(occ, 0, sizeof(uint64_t) * n, ctx->stream));
-    const int64_t grid = std::min<int64_t>(nb, (int64_t)ctx->num_sms * 32);
+    const int64_t grid = std::min<int64_t>(nb, (int64_t)ctx->num_sms * ctx->tune.fof_link_ctas_per_sm);
     RS_LAUNCH(ctx, "fof_occ", k_fof_occ, grid, T, 0, (const uint32_t *)n_cells, (const uint64_t *)cell_key,
               (const uint32_t *)table, occ);
 
@@ -724,7 +723,8 @@ rs_status fof_run(rs_ctx *ctx, const float *pos, int32_t stride, int64_t n, doub
         if (n_centres) RS_TRY(rs_read_i64(ctx, acnt + 1, 1, n_centres, "rs_fof3d_accel"));
     }
     RS_LAUNCH(ctx, "fof_rootmin", k_fof_rootmin, grid, T, 0, (const uint32_t *)n_cells,
-              (const uint32_t *)cell_start, (const uint32_t *)idx, parent, root_min, ctx->d_status);
+              (const uint32_t *)cell_start, (const uint32_t *)idx, parent, root_min,
+              rs_fault("timeout1") ? 1 : RS_SPIN_LIMIT, ctx->d_status);
     RS_LAUNCH(ctx, "fof_labels", k_fof_labels, nb, T, 0, n, (const uint32_t *)idx, (const uint32_t *)cell_of,
               parent, (const int *)root_min, labels, ctx->d_status);
     if (n_groups || n_tieband) {
@@ -830,6 +830,7 @@ extern "C" rs_status rs_group_sort(rs_ctx *ctx, const int32_t *labels, int64_t n
         RS_CUDA(ctx, cudaMemsetAsync(offsets, 0, sizeof(int64_t), ctx->stream));
         return RS_OK;
     }
+    RsStageGuard running(&ctx->in_gs);
     const int64_t T = 256, nb = ceil_div(n, T);
     RS_WS(ctx, uint32_t, count, WS_GS_COUNT, n);
     RS_WS(ctx, uint32_t, fl, WS_GS_FLAG, 4 * n + 8);

@@ -75,19 +75,13 @@ cudaError_t scratch_address(int device, void **out)
     return cudaSuccess;
 }
 
-// Coarse cells per side that rs_fof3d uses for (n, box, b): the same
-// arithmetic, repeated here so the table size can be checked before the call.
+// Coarse cells of the grid rs_fof3d builds for (n, box, b), from the grid
+// rule rs_fof3d itself uses, so the table size is checked before the call.
 bool coarse_cells(int64_t n, double box, double b, int64_t *cells)
 {
-    const double l = rs_linking_length(n, box, b);
-    if (!(l > 0)) return false;
-    const double u = 5.9604644775390625e-08;
-    const double gf_est = box * std::sqrt(3.0) / l + 16.0;
-    const double err = 2.0001 * u * gf_est * 1.01;
-    const double s_max = l * (1.0 - 1e-7) / (std::sqrt(3.0) * (1.0 + 2.0 * err));
-    const double gc = std::ceil(box / (4.0 * s_max));
-    if (!(gc < 2.0e6)) return false;
-    *cells = (int64_t)gc * (int64_t)gc * (int64_t)gc;
+    const FofGridSize gs = fof_grid_size(n, box, b);
+    if (!(gs.l > 0) || !(gs.gc < 2.0e6)) return false;
+    *cells = (int64_t)gs.gc * (int64_t)gs.gc * (int64_t)gs.gc;
     return true;
 }
 
@@ -111,10 +105,12 @@ extern "C" rs_status rs_fof3d_static(const float *pos, int32_t stride, int64_t n
 
     // A host-side context whose workspace slots already point into the
     // scratch array at their full capacity, so rs_fof3d never has a reason to
-    // allocate.  Its status words live in the scratch and on this stack.
+    // allocate, and is marked fixed: should a slot ever be too small, the
+    // call fails with RS_ERR_INTERNAL instead of allocating.  Its status words live in the scratch and on this stack.
     rs_ctx c;
     c.stream = (cudaStream_t)cuda_stream;
     c.device = device;
+    c.fixed_ws = 1;  // a slot that would need more room fails instead of allocating
     if (cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return RS_ERR_CUDA;
     unsigned char *p = (unsigned char *)base;

@@ -710,6 +710,9 @@ __global__ void __launch_bounds__(UT_WARPS * 32) k_ub_walk(int64_t njobs, const 
         }
     }
     phi += (double)acc;
+    // a walk that ran out of iterations with boxes still pending has a
+    // partial potential: record it like every other bounded loop
+    if (sp > 0 && lane == 0) dev_fail(st, DEV_TIMEOUT, 76, r);
     if (!have) return;
     ub_finish(tmem[a + m], r, phi * gm, vel, stride, vbulk, halo_id, hid, n_bound, bound_own, phi_own);
 }

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -82,6 +83,18 @@ struct rs_ctx {
     std::vector<rs_prof_rec> prof_recs;
     std::vector<cudaEvent_t> ev_free;
     int64_t launches = 0;
+    // the workspace slots are fixed regions set up by the caller (no device
+    // allocation allowed): a slot that is too small is an internal error
+    int fixed_ws = 0;
+    // set while a 3D FOF or group-sort call runs: its slots are in use and
+    // must not be released to make room (see rs_ws)
+    int in_fof = 0, in_gs = 0;
+    rs_tuning tune;  // launch choices (rs_set_tuning)
+    rs_ctx() { rs_tuning_default(&tune); }
+    // second stream and events for copies that overlap the kernels of the
+    // context's stream (rs_find_halos with host buffers); created on first use
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_io[3] = {nullptr, nullptr, nullptr};
 };
 
 // ---------------------------------------------------------------------------
@@ -90,14 +103,34 @@ struct rs_ctx {
 rs_status rs_fail(rs_ctx *ctx, rs_status s, const std::string &msg);
 rs_status rs_cuda_fail(rs_ctx *ctx, cudaError_t e, const char *where);
 // Device buffer of at least `bytes` for a slot; contents are kept while the
-// slot does not grow.  Returns nullptr (and records RS_ERR_OOM) on failure.
+// slot does not grow.  When the device is out of memory, the slots of the 3D
+// FOF and of the group sort (scratch of those calls only) are released if
+// neither call is running, and the allocation is tried once more.  Returns
+// nullptr (and records RS_ERR_OOM) on failure.
 void *rs_ws(rs_ctx *ctx, int slot, size_t bytes);
+// Total bytes of the context's workspace slots.
+size_t rs_ws_total(const rs_ctx *ctx);
+
+// Marks a 3D FOF or group-sort call as running for its scope.
+struct RsStageGuard {
+    int *flag;
+    explicit RsStageGuard(int *f) : flag(f) { *flag = 1; }
+    ~RsStageGuard() { *flag = 0; }
+};
 int rs_prof_begin(rs_ctx *ctx, const char *name);
 void rs_prof_end(rs_ctx *ctx, int rec);
 // Synchronises the stream and turns the device status word into an rs_status.
 rs_status rs_sync_check(rs_ctx *ctx, const char *where);
 // Copies `count` int64 values from device to host scratch and synchronises.
 rs_status rs_read_i64(rs_ctx *ctx, const void *dsrc, int count, int64_t *dst, const char *where);
+// Host-side fault injection for the failure-detection tests: true when the
+// environment variable RS_FAULT, a comma-separated list, names `site`.
+// Sites: "alloc" (every workspace allocation fails), "timeout1" (the 3D FOF
+// label pass runs with a bound of one step per find), "offsets" (rs_find_halos
+// corrupts the group offsets it passes to the refinement), "bracket" (the
+// sampled search bracket of every big node of odd rank is treated as failed,
+// which sends those nodes to the unbounded fallback search).
+bool rs_fault(const char *site);
 
 #define RS_TRY(expr)                         \
     do {                                     \
@@ -126,7 +159,7 @@ rs_status rs_read_i64(rs_ctx *ctx, const void *dsrc, int count, int64_t *dst, co
 
 #define RS_WS(ctx, T, var, slot, count)                                         \
     T *var = (T *)rs_ws((ctx), (slot), sizeof(T) * (size_t)((count) > 0 ? (count) : 1)); \
-    if (!var) return RS_ERR_OOM
+    if (!var) return (ctx)->fixed_ws ? RS_ERR_INTERNAL : RS_ERR_OOM
 
 __host__ __device__ static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -188,13 +221,34 @@ __device__ __forceinline__ double f64_mul(double a, double b) { return __dmul_rn
 __device__ __forceinline__ double f64_add(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double f64_sub(double a, double b) { return __dsub_rn(a, b); }
 
+// Fine cells per side of the 3D FOF grid for (n, box, b): the side s is the
+// largest with sqrt(3) s (1 + 2 err) < l, err being the float32 error of a
+// fine-cell coordinate in cell units (2.0001 u Gf), rounded down so that 4 Gc
+// cells fill the box.  Returns Gc (coarse cells per side; 0 when l <= 0) and
+// the estimate of Gf and err the caller checks the grid against.  Host only;
+// every caller of the 3D FOF grid uses it.
+struct FofGridSize {
+    double gc, gf_est, err, l;
+};
+static inline FofGridSize fof_grid_size(int64_t n, double box, double b)
+{
+    FofGridSize r{0.0, 0.0, 0.0, rs_linking_length(n, box, b)};
+    if (!(r.l > 0)) return r;
+    const double u = 5.9604644775390625e-08;  // 2^-24
+    r.gf_est = box * std::sqrt(3.0) / r.l + 16.0;
+    r.err = 2.0001 * u * r.gf_est * 1.01;
+    const double s_max = r.l * (1.0 - 1e-7) / (std::sqrt(3.0) * (1.0 + 2.0 * r.err));
+    r.gc = std::ceil(box / (4.0 * s_max));
+    return r;
+}
+
 // Lock-free union-find over int32 node ids: every root is the smallest id of
 // its set (the larger root is hooked under the smaller one with a CAS, after
 // the ECL-CC scheme of Jaiganesh & Burtscher 2018).  Loops are bounded; on
 // running out they record DEV_TIMEOUT and give up.
-__device__ __forceinline__ int uf_find(int *parent, int x, rs_dev_status *st)
+__device__ __forceinline__ int uf_find_n(int *parent, int x, rs_dev_status *st, int limit)
 {
-    for (int it = 0; it < RS_SPIN_LIMIT; it++) {
+    for (int it = 0; it < limit; it++) {
         int p = __ldcg(&parent[x]);
         if (p == x) return x;
         int g = __ldcg(&parent[p]);
@@ -203,6 +257,11 @@ __device__ __forceinline__ int uf_find(int *parent, int x, rs_dev_status *st)
     }
     dev_fail(st, DEV_TIMEOUT, 1, x);
     return x;
+}
+
+__device__ __forceinline__ int uf_find(int *parent, int x, rs_dev_status *st)
+{
+    return uf_find_n(parent, x, st, RS_SPIN_LIMIT);
 }
 
 __device__ __forceinline__ void uf_union(int *parent, int a, int b, rs_dev_status *st)

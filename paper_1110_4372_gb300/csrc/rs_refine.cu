@@ -1325,10 +1325,11 @@ __device__ __forceinline__ float w32_nn(const BvhView &V, const MemberStore &M, 
 // nearest-neighbour distances, one warp per job of 32 consecutive members
 // (one leaf): the leaf is held in registers, one member per lane, and its 32
 // queries are searched one after another
-__global__ void __launch_bounds__(W_WARPS * 32, 6) k_bvh_nn(LevelBufs L, WarpJobs J, NodeArrays nd,
+template <int MINB>
+__global__ void __launch_bounds__(W_WARPS * 32, MINB) k_bvh_nn(LevelBufs L, WarpJobs J, NodeArrays nd,
                                                          const int64_t *box_base, BoxStore B, MemberStore MS,
-                                                         const float *R2, const float *STOP, float *out,
-                                                         rs_dev_status *st)
+                                                         const float *R2, const float *STOP, int redo_failed,
+                                                         float *out, rs_dev_status *st)
 {
     __shared__ int si_s[W_WARPS][W_STACK];
     __shared__ float sd_s[W_WARPS][W_STACK];
@@ -1343,11 +1344,18 @@ __global__ void __launch_bounds__(W_WARPS * 32, 6) k_bvh_nn(LevelBufs L, WarpJob
     bvh_view(V, B, box_base[k], n);
     const MemberStore M = mem_shift(MS, first);
     // start from the node's radius when one is given (just above it, so a
-    // result at or above the start means "nothing within the radius")
-    const float start = R2 ? R2[k] * 1.00000095367431640625f : INFINITY;
-    // a query whose radius falls below the stop value is done: its member is
-    // certainly below the linking length and its exact value is not needed
-    const float stop = STOP ? STOP[k] : 0.f;
+    // result at or above the start means "nothing within the radius"); a
+    // query whose radius falls below the stop value is done: its member is
+    // certainly below the linking length and its exact value is not needed.
+    // With redo_failed, only the nodes whose bracket failed (R2 = -1) are
+    // searched again, unbounded.
+    float start = INFINITY, stop = 0.f;
+    if (redo_failed) {
+        if (!(R2[k] < 0.f)) return;
+    } else {
+        start = R2 ? R2[k] * 1.00000095367431640625f : INFINITY;
+        stop = STOP ? STOP[k] : 0.f;
+    }
     const int own = q0 / BVH_LEAF;
     const int mo = q0 + lane;
     const bool have = mo < n;
@@ -1582,7 +1590,8 @@ __device__ __forceinline__ int w32_link(const BvhView &V, const MemberStore &M, 
 // friends-of-friends at l, one warp per leaf of 32 consecutive members, pairs
 // with the candidate after the query in the node's member order; only
 // members with a neighbour within reach take part
-__global__ void __launch_bounds__(TQ, 5) k_bvh_link(LevelBufs L, NodeArrays nd, const int64_t *box_base,
+template <int MINB>
+__global__ void __launch_bounds__(TQ, MINB) k_bvh_link(LevelBufs L, NodeArrays nd, const int64_t *box_base,
                                                  BoxStore B, MemberStore MS, const float *dnn, int *parent,
                                                  rs_dev_status *st)
 {
@@ -1643,16 +1652,17 @@ __global__ void __launch_bounds__(TQ, 5) k_bvh_link(LevelBufs L, NodeArrays nd, 
 // for the linking length; if the k-th value is not within t_hi the level
 // falls back to the unbounded search, so the result is always exact.
 constexpr int SMP_MAX = 1024;       // sample size per node
-constexpr int SMP_MIN_NODE = 4096;  // smaller nodes are searched without a bracket
+// (nodes of at most rs_tuning::bracket_min members, 4096 by default, are
+// searched without a bracket)
 
 // (nodes that draw a member subset for the linking length search only the
 // subset, without a bracket)
-__global__ void k_smp_prep(const int *list, int K, NodeArrays nd, int64_t *ns, int sub_n)
+__global__ void k_smp_prep(const int *list, int K, NodeArrays nd, int64_t *ns, int sub_n, int min_node)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
     const int n = nd.count[list[k]];
-    ns[k] = (n > SMP_MIN_NODE && !(sub_n > 0 && n > sub_n)) ? SMP_MAX : 0;
+    ns[k] = (n > min_node && !(sub_n > 0 && n > sub_n)) ? SMP_MAX : 0;
 }
 
 // full-search warp jobs: every 32 consecutive members of every node
@@ -1725,15 +1735,23 @@ __global__ void k_smp_thresh(LevelBufs L, NodeArrays nd, const int64_t *soff, co
 
 // the level falls back to the full search when the float32 band around a
 // node's k-th value is not inside (stop, radius)
-__global__ void k_bracket_check(LevelBufs L, const float *R2, const float *STOP, int *fallback)
+// A node whose bracket did not hold gets R2 = -1: the fallback search
+// redoes that node only (force_odd, from the injected fault
+// RS_FAULT=bracket, fails every node of odd rank that has a bracket).
+__global__ void k_bracket_check(LevelBufs L, float *R2, const float *STOP, int *fallback, int force_odd)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= L.K) return;
     // the whole float32 band around the k-th value must lie inside the radius,
     // so no member that belongs in the band was cut off by it
     const float t32 = __uint_as_float(L.sel_prefix[k]);
-    if (!((double)t32 * (1.0 + 4.0 * RS_BAND) <= (double)R2[k])) atomicExch(fallback, 1);
-    if (!((double)t32 * (1.0 - 4.0 * RS_BAND) >= (double)STOP[k])) atomicExch(fallback, 1);
+    bool fail = !((double)t32 * (1.0 + 4.0 * RS_BAND) <= (double)R2[k]) ||
+                !((double)t32 * (1.0 - 4.0 * RS_BAND) >= (double)STOP[k]);
+    if (force_odd && (k & 1) && !isinf(R2[k])) fail = true;
+    if (fail) {
+        R2[k] = -1.f;
+        atomicExch(fallback, 1);
+    }
 }
 
 // ---- level-0 ordering: k-d splits at leaf-aligned medians ----
@@ -2412,6 +2430,28 @@ size_t tree_bytes(int64_t M, int64_t cap)
 
 }  // namespace
 
+// the big-node nearest-neighbour search, compiled for 5, 6 or 7 resident
+// blocks per SM (rs_tuning::nn_blocks_per_sm)
+static rs_status launch_nn(rs_ctx *ctx, const char *name, int64_t W, const LevelBufs &L, const WarpJobs &JF,
+                           const NodeArrays &nd, const int64_t *bo, const BoxStore &boxes, const MemberStore &ms,
+                           const float *R2, const float *STOP, int redo_failed, float *dnn)
+{
+    switch (ctx->tune.nn_blocks_per_sm) {
+    case 5:
+        RS_LAUNCH(ctx, name, k_bvh_nn<5>, ceil_div(W, W_WARPS), W_WARPS * 32, 0, L, JF, nd, bo, boxes, ms, R2, STOP,
+                  redo_failed, dnn, ctx->d_status);
+        break;
+    case 7:
+        RS_LAUNCH(ctx, name, k_bvh_nn<7>, ceil_div(W, W_WARPS), W_WARPS * 32, 0, L, JF, nd, bo, boxes, ms, R2, STOP,
+                  redo_failed, dnn, ctx->d_status);
+        break;
+    default:
+        RS_LAUNCH(ctx, name, k_bvh_nn<6>, ceil_div(W, W_WARPS), W_WARPS * 32, 0, L, JF, nd, bo, boxes, ms, R2, STOP,
+                  redo_failed, dnn, ctx->d_status);
+    }
+    return RS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
@@ -2565,11 +2605,11 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         RS_WS(ctx, uint32_t, v1, WS_SORT_V1, LM);
         int rbits = 0;
         while (rbits < 32 && ((uint64_t)(K - 1) >> rbits) != 0) rbits++;
-        if (level <= 1) {
+        if (level < ctx->tune.kd_levels) {
             // order each big node's members by k-d splits at leaf-aligned
-            // medians (levels 0 and 1, where most of the search work is);
-            // deeper levels keep this order through the stable child
-            // partition below
+            // medians (levels 0 and 1 by default, where most of the search
+            // work is); deeper levels keep this order through the stable
+            // child partition below
             int64_t maxn = 0;
             RS_TRY(rs_read_i64(ctx, tot + 3, 1, &maxn, "rs_refine6d"));
             RS_WS(ctx, int64_t, kw, WS_RF_MISC5, 2 * (K + 1) + 8);
@@ -2668,7 +2708,7 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         RS_WS(ctx, int64_t, ch, WS_RF_MISC4, 2 * (K + 1) + 8);
         int64_t *nsm = ch, *stot = ch + (K + 1);
         RS_LAUNCH(ctx, "rf_smp_prep", k_smp_prep, ceil_div(K, 256), 256, 0, (const int *)cur, (int)K, nd, nsm,
-                  (int)sub_n);
+                  (int)sub_n, (int)ctx->tune.bracket_min);
         RS_CUDA(ctx, cudaMemsetAsync(nsm + K, 0, sizeof(int64_t), ctx->stream));
         RS_TRY(rs_scan_i64(ctx, nsm, K + 1, stot));
         int64_t SS;
@@ -2706,8 +2746,7 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         JF.count = W;
         RS_LAUNCH(ctx, "rf_full_jobs", k_full_jobs, K, 128, 0, (const int *)cur, (int)K, nd, (const int64_t *)nw, jf,
                   jf + W, jf + 2 * W);
-        RS_LAUNCH(ctx, "rf_lvl_nn", k_bvh_nn, ceil_div(W, W_WARPS), W_WARPS * 32, 0, L, JF, nd, (const int64_t *)bo,
-                  boxes, ms, (const float *)R2, (const float *)STOP, dnn, ctx->d_status);
+        RS_TRY(launch_nn(ctx, "rf_lvl_nn", W, L, JF, nd, bo, boxes, ms, R2, STOP, 0, dnn));
         if (QN > 0)
             RS_LAUNCH(ctx, "rf_sub_nn", k_bvh_nn_list, ceil_div(QN, W_WARPS), W_WARPS * 32, 0, L, nd,
                       (const int64_t *)bo, boxes, ms, (const int2 *)sub_q, (const int *)sub_len, (int)qcap, dnn,
@@ -2717,15 +2756,14 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
             RS_LAUNCH(ctx, "rf_lvl_hist", k_lvl_hist, T, TQ, 0, L, nd, (const float *)dnn, pass);
             RS_LAUNCH(ctx, "rf_lvl_pick", k_lvl_pick, K, 32, 0, L, pass);
         }
-        RS_LAUNCH(ctx, "rf_bracket_check", k_bracket_check, ceil_div(K, 128), 128, 0, L, (const float *)R2,
-                  (const float *)STOP, fallback);
+        RS_LAUNCH(ctx, "rf_bracket_check", k_bracket_check, ceil_div(K, 128), 128, 0, L, R2,
+                  (const float *)STOP, fallback, rs_fault("bracket") ? 1 : 0);
         int64_t fo;
         RS_TRY(rs_read_i64(ctx, ctr + 6, 1, &fo, "rs_refine6d"));
         if ((fo >> 32) != 0) {
-            // the bracket did not hold for some node: unbounded search
-            RS_LAUNCH(ctx, "rf_lvl_nn_full", k_bvh_nn, ceil_div(W, W_WARPS), W_WARPS * 32, 0, L, JF, nd,
-                      (const int64_t *)bo, boxes, ms, (const float *)nullptr, (const float *)nullptr, dnn,
-                      ctx->d_status);
+            // the bracket did not hold for some node: unbounded search of
+            // those nodes (the others keep their values and selection)
+            RS_TRY(launch_nn(ctx, "rf_lvl_nn_full", W, L, JF, nd, bo, boxes, ms, R2, nullptr, 1, dnn));
             RS_LAUNCH(ctx, "rf_lvl_initk", k_lvl_initk, ceil_div(K, 128), 128, 0, L, nd, f, (int)sub_n);
             for (int pass = 0; pass < 3; pass++) {
                 RS_LAUNCH(ctx, "rf_lvl_hist", k_lvl_hist, T, TQ, 0, L, nd, (const float *)dnn, pass);
@@ -2743,8 +2781,19 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         RS_LAUNCH(ctx, "rf_lvl_iota", k_lvl_iota, T, TQ, 0, L, nd, uf, csize, cmin);
         RS_LAUNCH(ctx, "rf_bvh_linkbox", k_bvh_linkbox, K, 256, 0, L, nd, (const int64_t *)bo, boxes,
                   (const float4 *)wpos, (const float4 *)wvel, (const float *)dnn, uf, ctx->d_status);
-        RS_LAUNCH(ctx, "rf_lvl_link", k_bvh_link, T, TQ, 0, L, nd, (const int64_t *)bo, boxes, ms,
-                  (const float *)dnn, uf, ctx->d_status);
+        switch (ctx->tune.link_blocks_per_sm) {
+        case 4:
+            RS_LAUNCH(ctx, "rf_lvl_link", k_bvh_link<4>, T, TQ, 0, L, nd, (const int64_t *)bo, boxes, ms,
+                      (const float *)dnn, uf, ctx->d_status);
+            break;
+        case 6:
+            RS_LAUNCH(ctx, "rf_lvl_link", k_bvh_link<6>, T, TQ, 0, L, nd, (const int64_t *)bo, boxes, ms,
+                      (const float *)dnn, uf, ctx->d_status);
+            break;
+        default:
+            RS_LAUNCH(ctx, "rf_lvl_link", k_bvh_link<5>, T, TQ, 0, L, nd, (const int64_t *)bo, boxes, ms,
+                      (const float *)dnn, uf, ctx->d_status);
+        }
         RS_LAUNCH(ctx, "rf_lvl_comp", k_lvl_comp, T, TQ, 0, L, nd, (const int *)widx, uf, csize, cmin,
                   ctx->d_status);
         // reorder: children first, by smallest particle index, then the rest
@@ -2781,14 +2830,16 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         const size_t smid = sizeof(SmallShared<MID_N, MID_THREADS>);
         RS_CUDA(ctx, cudaFuncSetAttribute(kbig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbig));
         RS_CUDA(ctx, cudaFuncSetAttribute(kmid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smid));
-        RS_LAUNCH(ctx, "rf_small_subtree", kbig, (int64_t)ctx->num_sms * 2, SMALL_THREADS, sbig, (const int *)small_q,
-                  (const int *)(ctr + 2), ctr + 3, wpos, wvel, widx, MID_N, mid_q, ctr + 11, nd, box, f, (int)min_n,
-                  ctx->d_status);
-        RS_LAUNCH(ctx, "rf_mid_subtree", kmid, (int64_t)ctx->num_sms * 8, MID_THREADS, smid, (const int *)mid_q,
-                  (const int *)(ctr + 11), ctr + 12, wpos, wvel, widx, TINY_N, tiny_q, ctr + 8, nd, box, f,
-                  (int)min_n, ctx->d_status);
+        const rs_tuning &tu = ctx->tune;
+        RS_LAUNCH(ctx, "rf_small_subtree", kbig, (int64_t)ctx->num_sms * tu.small_ctas_per_sm, SMALL_THREADS, sbig,
+                  (const int *)small_q, (const int *)(ctr + 2), ctr + 3, wpos, wvel, widx,
+                  std::min(tu.mid_max, MID_N), mid_q, ctr + 11, nd, box, f, (int)min_n, ctx->d_status);
+        RS_LAUNCH(ctx, "rf_mid_subtree", kmid, (int64_t)ctx->num_sms * tu.mid_ctas_per_sm, MID_THREADS, smid,
+                  (const int *)mid_q, (const int *)(ctr + 11), ctr + 12, wpos, wvel, widx,
+                  std::min(tu.tiny_max, TINY_N), tiny_q, ctr + 8, nd, box, f, (int)min_n, ctx->d_status);
     }
-    RS_LAUNCH(ctx, "rf_tiny_subtree", k_tiny_subtree, (int64_t)ctx->num_sms * 8, TINY_WARPS * 32, 0,
+    RS_LAUNCH(ctx, "rf_tiny_subtree", k_tiny_subtree, (int64_t)ctx->num_sms * ctx->tune.tiny_ctas_per_sm,
+              TINY_WARPS * 32, 0,
               (const int *)tiny_q, (const int *)(ctr + 8), ctr + 9, (const float4 *)wpos, (const float4 *)wvel, widx,
               nd, box, f, (int)min_n, ctx->d_status);
 

@@ -35,6 +35,15 @@ class rs_params(C.Structure):
                 ("nn_seed", C.c_uint64)]
 
 
+class rs_tuning(C.Structure):
+    _fields_ = [(k, C.c_int32) for k in ("link_blocks_per_sm", "nn_blocks_per_sm", "kd_levels", "bracket_min",
+                                         "mid_max", "tiny_max", "small_ctas_per_sm", "mid_ctas_per_sm",
+                                         "tiny_ctas_per_sm", "fof_link_ctas_per_sm")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class rs_stats(C.Structure):
     _fields_ = [("n_fof_groups", C.c_int64), ("n_members", C.c_int64), ("n_nodes", C.c_int64),
                 ("n_levels", C.c_int32), ("n_seeds", C.c_int64), ("n_halos", C.c_int64),
@@ -83,6 +92,10 @@ def _declare(lib):
         "rs_profile_count": (i32, [P]),
         "rs_profile_read": (C.c_int, [P, i32, C.POINTER(C.c_char_p), C.POINTER(i64), C.POINTER(f64)]),
         "rs_launch_count": (i64, [P]),
+        "rs_workspace_bytes": (i64, [P]),
+        "rs_tuning_default": (None, [C.POINTER(rs_tuning)]),
+        "rs_set_tuning": (C.c_int, [P, C.POINTER(rs_tuning)]),
+        "rs_get_tuning": (C.c_int, [P, C.POINTER(rs_tuning)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -432,6 +445,35 @@ def rs_profile_read(ctx: Context) -> dict:
 
 def rs_launch_count(ctx: Context) -> int:
     return int(lib().rs_launch_count(ctx.handle))
+
+
+def rs_tuning_default() -> dict:
+    t = rs_tuning()
+    lib().rs_tuning_default(C.byref(t))
+    return t.as_dict()
+
+
+def rs_get_tuning(ctx: Context) -> dict:
+    t = rs_tuning()
+    ctx.check(lib().rs_get_tuning(ctx.handle, C.byref(t)))
+    return t.as_dict()
+
+
+def rs_set_tuning(ctx: Context, **fields) -> dict:
+    """Sets the named launch choices (the rest keep their current values);
+    returns the context's whole tuning."""
+    t = rs_tuning()
+    ctx.check(lib().rs_get_tuning(ctx.handle, C.byref(t)))
+    for k, v in fields.items():
+        if k not in t.as_dict():
+            raise KeyError(k)
+        setattr(t, k, int(v))
+    ctx.check(lib().rs_set_tuning(ctx.handle, C.byref(t)))
+    return t.as_dict()
+
+
+def rs_workspace_bytes(ctx: Context) -> int:
+    return int(lib().rs_workspace_bytes(ctx.handle))
 
 
 def mean_spacing(n: int, box: float) -> float:

@@ -255,11 +255,16 @@ class GroupCatalogue:
         return int(self.pos.shape[0])
 
 
-def _group(g, cfg, seed, cs, table):
-    """One group from its own substream (so groups can be drawn in any chunks)."""
+def _group_rng_and_size(g, cfg, seed):
+    """Group g's substream and its particle count, the substream's first draw."""
     rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, g])))
     n = int(np.exp(rng.uniform(np.log(cfg["nmin"]), np.log(cfg["nmax"] + 1.0))))
-    n = min(max(n, cfg["nmin"]), cfg["nmax"])
+    return rng, min(max(n, cfg["nmin"]), cfg["nmax"])
+
+
+def _group(g, cfg, seed, cs, table):
+    """One group from its own substream (so groups can be drawn in any chunks)."""
+    rng, n = _group_rng_and_size(g, cfg, seed)
     k = int(rng.integers(0, cfg["max_subs"] + 1))
     sub_n = np.floor(rng.uniform(0.01, 0.10, size=k) * n).astype(np.int64)
     sub_n = sub_n[sub_n >= 10]
@@ -313,6 +318,18 @@ def groups(name: str = "c4s", *, first: int = 0, count: int | None = None,
     truth = np.concatenate([q[2] for q in parts])
     return GroupCatalogue(pos=np.ascontiguousarray(pos), vel=np.ascontiguousarray(vel), box=L, offsets=offsets,
                           truth=truth)
+
+
+def group_sizes(name: str = "c4s", *, first: int = 0, count: int | None = None,
+                seed: int | None = None) -> np.ndarray:
+    """Particle counts of groups first .. first+count-1 of the workload
+    ``name``, without drawing the particles (int64)."""
+    cfg = GROUP_CONFIGS[name]
+    if seed is None:
+        seed = BASE_SEED + 4
+    if count is None:
+        count = cfg["n_groups"] - first
+    return np.array([_group_rng_and_size(g, cfg, seed)[1] for g in range(first, first + count)], np.int64)
 
 
 def uniform(n: int, box: float, seed: int, vel_sigma: float = 20.0) -> Catalogue:

@@ -46,3 +46,28 @@ def test_per_group_sample_selection():
     assert set(np.argsort(sizes)[::-1][:20]) <= set(a.tolist())
     c, _ = bench.sample_groups(sizes, 10000, 7)
     assert np.array_equal(c, np.arange(5000))
+
+
+def test_stream_chunk_plan():
+    """The streamed batching benchmark's plan: chunks of whole consecutive
+    groups within the particle cap (or one oversized group alone), tasks
+    tiling each chunk, every group exactly once."""
+    import importlib.util
+    import numpy as np
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    sizes = np.random.default_rng(5).integers(20, 5000, 3000)
+    sizes[100] = 50_000  # larger than a chunk
+    chunks, tasks, tchunk = bench.plan_chunks(sizes, 40_000, task_particles=7000)
+    assert chunks[0][0] == 0 and chunks[-1][1] == len(sizes)
+    for (a, b), (c, d) in zip(chunks, chunks[1:]):
+        assert b == c
+    for a, b in chunks:
+        assert sizes[a:b].sum() <= 40_000 or b - a == 1
+    covered = []
+    for (a, b), k in zip(tasks, tchunk):
+        assert chunks[k][0] <= a < b <= chunks[k][1]
+        covered += list(range(a, b))
+    assert covered == list(range(len(sizes)))
+    assert bench.plan_chunks(np.zeros(0, np.int64), 10) == ([], [], [])

@@ -1,5 +1,6 @@
-"""Parity at the benchmark's full size (134M particles, the same calls the
-benchmark times), on sampled outputs the oracle can compute one by one:
+"""Parity at the benchmark's full size (134M particles, and 1.07B with
+RS_TEST_C5=1; the same calls the benchmark times), on sampled outputs the
+oracle can compute one by one:
 
 * 3D groups: the member set of the group of sampled particles, found by the
   oracle's breadth-first search over the whole box, equals the CUDA label
@@ -12,6 +13,8 @@ benchmark times), on sampled outputs the oracle can compute one by one:
   member), child and tie-band counts and every halo id must match exactly,
   with sigma, centre and linking length within 1e-6 relative.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -30,11 +33,16 @@ MAX_GROUP = 60000
 LARGE_MIN, LARGE_MAX = 200_000, 450_000
 
 
-@pytest.fixture(scope="module")
-def full():
+@pytest.fixture(scope="module", params=["c3", "c5"])
+def full(request):
+    """The 134M-particle workload; the 1.07B-particle one (c5) only when
+    RS_TEST_C5=1, since generating it and the oracle's grid over it take
+    about a quarter of an hour on the host."""
+    if request.param == "c5" and os.environ.get("RS_TEST_C5") != "1":
+        pytest.skip("the 1.07B-particle case runs with RS_TEST_C5=1")
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
     from paper_1110_4372_gb300 import rsgpu
-    cat = synth.generate("c3")
+    cat = synth.generate(request.param)
     ctx = rsgpu.Context()
     pos = torch.from_numpy(cat.pos).cuda()
     vel = torch.from_numpy(cat.vel).cuda()

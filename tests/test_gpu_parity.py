@@ -336,10 +336,16 @@ def test_find_halos_host_and_device(rs, ctx):
     assert np.array_equal(lab.cpu().numpy(), o["labels"])
     hp = torch.from_numpy(c.pos).pin_memory()
     vp = torch.from_numpy(c.vel).pin_memory()
-    hid2, _, st2 = rs.rs_find_halos(ctx, hp, vp, c.box)
+    lab_h = torch.full((c.n,), -5, dtype=torch.int32).pin_memory()
+    hid2, _, st2 = rs.rs_find_halos(ctx, hp, vp, c.box, fof_labels=lab_h)
     assert not hid2.is_cuda
     assert np.array_equal(hid2.numpy(), o["halo_id"])
+    assert np.array_equal(lab_h.numpy(), o["labels"])  # copied back while the refinement ran
     assert st2["n_halos"] == len(o["halos"].id) == st["n_halos"]
+    # repeated host-buffer calls reuse the second stream and its events
+    for _ in range(2):
+        hid3, _, _ = rs.rs_find_halos(ctx, hp, vp, c.box)
+        assert np.array_equal(hid3.numpy(), o["halo_id"])
 
 
 def test_empty_inputs(rs, ctx):
@@ -379,3 +385,80 @@ def test_full_path_c2_subset_10000(rs, ctx):
     length from a random 10,000-particle subset (Sec. 3.2)."""
     matched, tie_nodes, info = _check_all(rs, ctx, synth.generate("c2"), sub_n=10000, sub_seed=11104372)
     assert matched == info.n_nodes > 5000
+
+
+@pytest.mark.slow
+def test_batching_stress_groups_c4s(rs, ctx):
+    """The independent-group batching workload (small case of its recipe:
+    NFW hosts with co-spatial, velocity-offset subhalos, Sec. 2.2 / Fig. 2),
+    first 400 groups given straight to rs_refine6d as group offsets (no 3D
+    FOF): the node tree equals the oracle's exactly, and so do the seed
+    merge and assignment at the recipe's density."""
+    g = synth.groups("c4s", first=0, count=400)
+    pos = torch.from_numpy(g.pos).cuda()
+    vel = torch.from_numpy(g.vel).cuda()
+    perm = torch.arange(g.n, dtype=torch.int32, device="cuda")
+    off = torch.from_numpy(g.offsets).cuda()
+    tree = rs.rs_refine6d(ctx, pos, vel, g.box, perm, off)
+    t = oracle.refine(g.pos, g.vel, g.box, np.arange(g.n, dtype=np.int32), g.offsets)
+    matched, _ = compare_trees(gpu_tree_dict(tree), oracle_tree_dict(t), g.box)
+    assert matched == t.n_nodes == tree.info().n_nodes > 400
+    assert tree.info().n_tieband == int(t.tie.sum())
+    hid, nh = rs.rs_assign(ctx, tree, pos, vel, g.box, rs.params(nbar=synth.GROUP_NBAR))
+    hid_o, halos = oracle.assign(t, g.n, g.box, 360.0, synth.GROUP_NBAR)
+    assert np.array_equal(hid.cpu().numpy(), hid_o) and nh == len(halos.id)
+
+
+OTHER_TUNING = dict(link_blocks_per_sm=4, nn_blocks_per_sm=7, kd_levels=1, bracket_min=2048, mid_max=128,
+                    tiny_max=16, small_ctas_per_sm=1, mid_ctas_per_sm=4, tiny_ctas_per_sm=12, fof_link_ctas_per_sm=8)
+
+
+def test_launch_choices_change_no_result(rs):
+    """Every launch choice of rs_tuning changes which CTA or warp does which
+    work, never a result: the whole path under choices different from the
+    defaults still matches the oracle exactly."""
+    ctx2 = rs.Context()
+    t = rs.rs_set_tuning(ctx2, **OTHER_TUNING)
+    assert t == dict(rs.rs_tuning_default(), **OTHER_TUNING) == rs.rs_get_tuning(ctx2)
+    for cat in (_big_catalogue(), synth.generate("c1")):
+        _check_all(rs, ctx2, cat)
+    ctx2.close()
+
+
+def test_tuning_rejects_out_of_range(rs, ctx):
+    before = rs.rs_get_tuning(ctx)
+    for bad in (dict(link_blocks_per_sm=3), dict(kd_levels=4), dict(mid_max=300), dict(tiny_max=33),
+                dict(bracket_min=100), dict(fof_link_ctas_per_sm=0)):
+        with pytest.raises(rs.RsError):
+            rs.rs_set_tuning(ctx, **bad)
+    assert rs.rs_get_tuning(ctx) == before
+
+
+def test_bracket_fallback_redoes_only_failed_nodes_exactly(rs, monkeypatch):
+    """Big nodes (above 4096 members) search within a sampled bracket of
+    the linking length; a node whose bracket does not hold is searched again
+    without it.  With the injected fault RS_FAULT=bracket every bracketed
+    node of odd rank takes that path while the others keep their bracketed
+    values: the tree still equals the oracle's exactly."""
+    rng = np.random.default_rng(9)
+    box = 40.0
+    parts, vels = [], []
+    for c in range(5):
+        centre = rng.random(3) * 30 + 5
+        p, v = synth.blob(rng, 5000 + 300 * c, centre, rng.standard_normal(3) * 100, 0.2, 80.0)
+        parts.append(p)
+        vels.append(v)
+    pos = synth.wrap(np.vstack(parts), box)
+    vel = np.vstack(vels).astype(np.float32)
+    n = len(pos)
+    cat = synth.Catalogue(pos=pos, vel=vel, box=box, truth=np.zeros(n, np.int32),
+                          comp_parent=np.zeros(0, np.int32), comp_n=np.zeros(0))
+    monkeypatch.setenv("RS_FAULT", "bracket")
+    ctx2 = rs.Context()
+    _check_all(rs, ctx2, cat)
+    p, v = cuda_inputs(cat)
+    _, _, st = rs.rs_find_halos(ctx2, p, v, cat.box)
+    assert st["n_fallback_levels"] >= 1
+    monkeypatch.delenv("RS_FAULT")
+    _, _, st = rs.rs_find_halos(ctx2, p, v, cat.box)
+    assert st["n_fallback_levels"] == 0

@@ -60,3 +60,12 @@ def test_independent_groups_recipe_and_chunks():
             assert 0.7 < dv < 3.3
             checked += 1
     assert checked >= 3
+
+
+def test_group_sizes_without_drawing_particles():
+    """The size-only draw equals the sizes of the drawn groups (the streamed
+    batching benchmark plans its chunks from it)."""
+    g = synth.groups("c4s", first=17, count=9)
+    assert np.array_equal(synth.group_sizes("c4s", first=17, count=9), np.diff(g.offsets))
+    s = synth.group_sizes("c4", first=0, count=2000)
+    assert s.min() >= 20 and s.max() <= 500_000

@@ -54,3 +54,25 @@ def test_no_alloc_fof_rejects_oversize():
     st = fn(C.c_void_p(pos.data_ptr()), 3, n, 20.0, 0.28, C.c_void_p(out.data_ptr()), None)
     assert st == 5  # RS_ERR_TOO_LARGE
     assert fn(C.c_void_p(pos.data_ptr()), 3, 1000, 20.0, 0.01, C.c_void_p(out.data_ptr()), None) == 5
+
+
+def test_no_alloc_fof_leaves_device_memory_unchanged():
+    """After the first call on the device (which loads the library's device
+    code and its scratch array), further calls change the device's free
+    memory by nothing: they allocate nothing."""
+    rsgpu, fn = _static_fn()
+    cat = synth.generate("c1", seed=77, n=20000, box=10.0 * (20000 / 32768) ** (1 / 3), n_halos=20)
+    pos = torch.from_numpy(cat.pos).cuda()
+    out = torch.empty(cat.n, dtype=torch.int32, device="cuda")
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    args = (C.c_void_p(pos.data_ptr()), 3, cat.n, cat.box, 0.28, C.c_void_p(out.data_ptr()), stream)
+    assert fn(*args) == 0
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        assert fn(*args) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    ctx = rsgpu.Context()
+    ref, _, _ = rsgpu.rs_fof3d(ctx, pos, cat.box, 0.28)
+    assert torch.equal(out, ref)
