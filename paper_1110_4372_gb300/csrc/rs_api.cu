@@ -40,7 +40,9 @@ static rs_status find_halos(rs_ctx *ctx, const float *pos, const float *vel, int
         ev_vel = ctx->ev_io[0];
         ev_lab = ctx->ev_io[1];
         ev_lab_done = ctx->ev_io[2];
+        const int pr = rs_prof_begin(ctx, "io_h2d_pos");
         RS_CUDA(ctx, cudaMemcpyAsync(p, pos, in_bytes, cudaMemcpyHostToDevice, ctx->stream));
+        rs_prof_end(ctx, pr);
         // the second stream starts after everything already on the context's
         // stream (nothing may still read the velocity workspace)
         RS_CUDA(ctx, cudaEventRecord(ev_lab, ctx->stream));
@@ -75,7 +77,11 @@ static rs_status find_halos(rs_ctx *ctx, const float *pos, const float *vel, int
         static const int64_t bad = -1;
         RS_CUDA(ctx, cudaMemcpy(offsets + 1, &bad, sizeof(int64_t), cudaMemcpyHostToDevice));
     }
-    if (host_buffers) RS_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ev_vel, 0));
+    if (host_buffers) {
+        const int pr = rs_prof_begin(ctx, "io_wait_vel");
+        RS_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ev_vel, 0));
+        rs_prof_end(ctx, pr);
+    }
     rs_tree *tree = nullptr;
     RS_TRY(rs_refine6d_sampled(ctx, dpos, dvel, stride, n, box, perm, offsets, G, params->f, params->min_n,
                                params->nn_subset, params->nn_seed, &tree));
@@ -95,7 +101,9 @@ static rs_status find_halos(rs_ctx *ctx, const float *pos, const float *vel, int
             stats->n_fallback_levels = tree->n_fallback_levels;
         }
         if (host_buffers) {
+            const int pr = rs_prof_begin(ctx, "io_d2h_halo");
             cudaError_t e = cudaMemcpyAsync(halo_id, hid, ob, cudaMemcpyDeviceToHost, ctx->stream);
+            rs_prof_end(ctx, pr);
             if (e == cudaSuccess && fof_labels) e = cudaStreamWaitEvent(ctx->stream, ev_lab_done, 0);
             if (e != cudaSuccess) s = rs_cuda_fail(ctx, e, "rs_find_halos: copy out");
         } else if (fof_labels) {

@@ -689,7 +689,7 @@ rs_status large_rdyn(rs_ctx *ctx, AsBufs A, int H, const int *root_of_rank, cons
     int bits = 32;
     while (bits < 64 && ((uint64_t)(NL - 1) >> (bits - 32)) != 0) bits++;
     bool alt = false;
-    RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, total, bits, &alt));
+    RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, total, bits, &alt, "sort_as"));
     RS_LAUNCH(ctx, "as_large_max", k_as_large_max, ceil_div(total, 256), 256, 0, (long long)total,
               (const long long *)lsize, (const unsigned long long *)(alt ? k1 : k0), (const unsigned *)(alt ? v1 : v0),
               (const double *)r64, bb);
@@ -748,7 +748,7 @@ extern "C" rs_status rs_assign_ex(rs_ctx *ctx, const rs_tree *t, const float *po
     int bits = 0;
     while (bits < 32 && ((uint64_t)(t->n_members > 0 ? t->n_members - 1 : 0) >> bits) != 0) bits++;
     bool alt = false;
-    RS_TRY(rs_radix_sort_u32(ctx, k0, k1, v0, v1, L, bits, &alt));
+    RS_TRY(rs_radix_sort_u32(ctx, k0, k1, v0, v1, L, bits, &alt, "sort_as"));
     AsBufs A;
     A.L = L;
     A.leaf_first = alt ? k1 : k0;

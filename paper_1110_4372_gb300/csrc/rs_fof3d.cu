@@ -653,7 +653,7 @@ rs_status fof_run(rs_ctx *ctx, const float *pos, int32_t stride, int64_t n, doub
     RS_WS(ctx, uint32_t, v1, WS_SORT_V1, n);
     RS_LAUNCH(ctx, "fof_keys", k_fof_keys, nb, T, 0, pos, stride, n, g, k0, v0, ctx->d_status);
     bool alt = false;
-    RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, n, key_bits(g), &alt));
+    RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, n, key_bits(g), &alt, "sort_fof"));
     uint64_t *keys = alt ? k1 : k0;
     uint32_t *idx = alt ? v1 : v0;
 
@@ -861,7 +861,7 @@ extern "C" rs_status rs_group_sort(rs_ctx *ctx, const int32_t *labels, int64_t n
     int bits = 0;
     while (bits < 32 && ((uint64_t)(G > 0 ? G - 1 : 0) >> bits) != 0) bits++;
     bool alt = false;
-    RS_TRY(rs_radix_sort_u32(ctx, k0, k1, v0, vtmp, Mm, bits, &alt));
+    RS_TRY(rs_radix_sort_u32(ctx, k0, k1, v0, vtmp, Mm, bits, &alt, "sort_gs"));
     if (alt)
         RS_CUDA(ctx, cudaMemcpyAsync(perm, vtmp, sizeof(uint32_t) * Mm, cudaMemcpyDeviceToDevice, ctx->stream));
     RS_CUDA(ctx, cudaMemsetAsync(offsets, 0, sizeof(int64_t) * (G + 1), ctx->stream));

@@ -174,10 +174,11 @@ constexpr int64_t RS_SORT_TILE = 2048;
 // Stable LSD radix sort of (key, value) pairs on key bits [0, nbits).  The
 // caller provides both ping-pong buffers; *out_in_alt says whether the
 // sorted data ended in (k1, v1).
+// `tag` names the launches for the per-kernel profile (tag_hist, tag_scatter).
 rs_status rs_radix_sort_u64(rs_ctx *ctx, uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, int64_t n,
-                            int nbits, bool *out_in_alt);
+                            int nbits, bool *out_in_alt, const char *tag = "sort");
 rs_status rs_radix_sort_u32(rs_ctx *ctx, uint32_t *k0, uint32_t *k1, uint32_t *v0, uint32_t *v1, int64_t n,
-                            int nbits, bool *out_in_alt);
+                            int nbits, bool *out_in_alt, const char *tag = "sort");
 
 // ---------------------------------------------------------------------------
 // Device helpers

@@ -1083,25 +1083,43 @@ __device__ __forceinline__ float point_box_d2(float4 p, float4 v, const Box6 &b,
     return (gx * gx + gy * gy + gz * gz) * m.ax + (gu * gu + gv * gv + gw * gw) * m.av;
 }
 
+// A node's hierarchy: its boxes and, per level, the first box (off) and the
+// box count (cnt).  The two small per-level tables live in shared memory
+// the caller provides (2 BVH_MAXH ints): the searches index them by a
+// run-time level, which from registers would put them in local memory.
 struct BvhView {
     BoxStore S;
     int nl, H;
-    int off[BVH_MAXH];
-    int cnt[BVH_MAXH];
+    const int *off;
+    const int *cnt;
 };
 
-__device__ __forceinline__ void bvh_view(BvhView &V, const BoxStore &B, int64_t base, int n)
+__device__ __forceinline__ void bvh_fill(int *lv, int nl)
+{
+    int o = 0, c = nl;
+    for (int h = 0; h < BVH_MAXH; h++) {
+        lv[h] = o;
+        lv[BVH_MAXH + h] = c;
+        o += c;
+        c = (c + 31) >> BVH_LOG;
+    }
+}
+
+__device__ __forceinline__ void bvh_set(BvhView &V, const BoxStore &B, int64_t base, int n, const int *lv)
 {
     V.S = box_shift(B, base);
     V.nl = (int)ceil_div(n, BVH_LEAF);
     V.H = min(bvh_levels(V.nl), BVH_MAXH);  // n <= 2^26 members per node (checked on the host): H <= 6
-    int o = 0, c = V.nl;
-    for (int h = 0; h < BVH_MAXH; h++) {
-        V.off[h] = o;
-        V.cnt[h] = c;
-        o += c;
-        c = (c + 31) >> BVH_LOG;
-    }
+    V.off = lv;
+    V.cnt = lv + BVH_MAXH;
+}
+
+// the view for a whole warp; lv is the warp's own shared table
+__device__ __forceinline__ void bvh_view(BvhView &V, const BoxStore &B, int64_t base, int n, int *lv)
+{
+    if (lane_id() == 0) bvh_fill(lv, (int)ceil_div(n, BVH_LEAF));
+    __syncwarp();
+    bvh_set(V, B, base, n, lv);
 }
 
 // ---- dense boxes at the linking length ----
@@ -1168,8 +1186,11 @@ __global__ void __launch_bounds__(256) k_bvh_linkbox(LevelBufs L, NodeArrays nd,
     const Metric6 met = L.met[k];
     const LinkLim lm = link_lim(L.l2[k]);
     const float lim = (float)(L.l2[k] * RS_CLIQUE_MARGIN);
+    __shared__ int lv_s[2 * BVH_MAXH];
+    if (threadIdx.x == 0) bvh_fill(lv_s, (int)ceil_div(n, BVH_LEAF));
+    __syncthreads();
     BvhView V;
-    bvh_view(V, B, box_base[k], n);
+    bvh_set(V, B, box_base[k], n, lv_s);
     // leaves; the flag holds "every member can have a friend" until the end
     for (int i = threadIdx.x; i < V.nl; i += blockDim.x) {
         Box6 b = box_empty();
@@ -1333,6 +1354,7 @@ __global__ void __launch_bounds__(W_WARPS * 32, MINB) k_bvh_nn(LevelBufs L, Warp
 {
     __shared__ int si_s[W_WARPS][W_STACK];
     __shared__ float sd_s[W_WARPS][W_STACK];
+    __shared__ int lv_s[W_WARPS][2 * BVH_MAXH];
     const int w = warp_id(), lane = lane_id();
     const int64_t gw = (int64_t)blockIdx.x * W_WARPS + w;
     if (gw >= J.count) return;
@@ -1341,7 +1363,7 @@ __global__ void __launch_bounds__(W_WARPS * 32, MINB) k_bvh_nn(LevelBufs L, Warp
     if (q0 >= n) return;
     const Metric6 met = L.met[k];
     BvhView V;
-    bvh_view(V, B, box_base[k], n);
+    bvh_view(V, B, box_base[k], n, lv_s[w]);
     const MemberStore M = mem_shift(MS, first);
     // start from the node's radius when one is given (just above it, so a
     // result at or above the start means "nothing within the radius"); a
@@ -1380,6 +1402,7 @@ __global__ void __launch_bounds__(W_WARPS * 32) k_bvh_nn_sample(LevelBufs L, Nod
 {
     __shared__ int si_s[W_WARPS][W_STACK];
     __shared__ float sd_s[W_WARPS][W_STACK];
+    __shared__ int lv_s[W_WARPS][2 * BVH_MAXH];
     const int w = warp_id(), lane = lane_id();
     const int k = blockIdx.y;
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
@@ -1389,7 +1412,7 @@ __global__ void __launch_bounds__(W_WARPS * 32) k_bvh_nn_sample(LevelBufs L, Nod
     const int q = (int)(((int64_t)s * n) / S);
     const Metric6 met = L.met[k];
     BvhView V;
-    bvh_view(V, B, box_base[k], n);
+    bvh_view(V, B, box_base[k], n, lv_s[w]);
     const MemberStore M = mem_shift(MS, first);
     float4 pq, vq, pm = make_float4(0, 0, 0, 0), vm = pm;
     mem_get(M, q, pq, vq);
@@ -1409,6 +1432,7 @@ __global__ void __launch_bounds__(W_WARPS * 32) k_bvh_nn_list(LevelBufs L, NodeA
 {
     __shared__ int si_s[W_WARPS][W_STACK];
     __shared__ float sd_s[W_WARPS][W_STACK];
+    __shared__ int lv_s[W_WARPS][2 * BVH_MAXH];
     const int w = warp_id(), lane = lane_id();
     const int64_t s = (int64_t)blockIdx.x * W_WARPS + w;
     if (s >= min(*qlen, cap)) return;
@@ -1417,7 +1441,7 @@ __global__ void __launch_bounds__(W_WARPS * 32) k_bvh_nn_list(LevelBufs L, NodeA
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
     const Metric6 met = L.met[k];
     BvhView V;
-    bvh_view(V, B, box_base[k], n);
+    bvh_view(V, B, box_base[k], n, lv_s[w]);
     const MemberStore M = mem_shift(MS, first);
     float4 pq, vq, pm = make_float4(0, 0, 0, 0), vm = pm;
     mem_get(M, q, pq, vq);
@@ -1597,6 +1621,7 @@ __global__ void __launch_bounds__(TQ, MINB) k_bvh_link(LevelBufs L, NodeArrays n
 {
     __shared__ int si_s[TQ / 32][LK_STACK];
     __shared__ int lf_s[TQ / 32][LK_LEAVES];
+    __shared__ int lv_s[TQ / 32][2 * BVH_MAXH];
     const int w = warp_id(), lane = lane_id();
     const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x] + 32 * w;
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
@@ -1617,7 +1642,7 @@ __global__ void __launch_bounds__(TQ, MINB) k_bvh_link(LevelBufs L, NodeArrays n
     float4 po = make_float4(0, 0, 0, 0), vo = po;
     if (have) mem_get(M, mo, po, vo);
     BvhView V;
-    bvh_view(V, B, box_base[k], n);
+    bvh_view(V, B, box_base[k], n, lv_s[w]);
     const int own = q0 / BVH_LEAF;
     int tie = 0;
     while (rem) {
@@ -2178,6 +2203,7 @@ __global__ void __launch_bounds__(W_WARPS * 32) k_lvl_band_exact(LevelBufs L, No
                                                                  rs_dev_status *st)
 {
     __shared__ int si_s[W_WARPS][W_STACK];
+    __shared__ int lv_s[W_WARPS][2 * BVH_MAXH];
     const int w = warp_id(), lane = lane_id();
     const int b = blockIdx.x * W_WARPS + w;
     if (b >= *L.band_len) return;
@@ -2190,7 +2216,7 @@ __global__ void __launch_bounds__(W_WARPS * 32) k_lvl_band_exact(LevelBufs L, No
     mem_get(M, q, pq, vq);
     const float lim = dnn[s] * (float)(1.0 + 2.0 * RS_BAND);
     BvhView V;
-    bvh_view(V, B, box_base[k], n);
+    bvh_view(V, B, box_base[k], n, lv_s[w]);
     const int own = q / BVH_LEAF;
     double best = INFINITY;
     {
@@ -2628,7 +2654,7 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
                 RS_LAUNCH(ctx, "rf_kd_keys", k_kd_keys, T, TQ, 0, L, nd, (const int64_t *)kseg, (const float4 *)wpos,
                           (const float4 *)wvel, vsorted, (unsigned long long *)k0, v0, r);
                 bool kalt = false;
-                RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, LM, 16 + sbits, &kalt));
+                RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, LM, 16 + sbits, &kalt, "sort_kd"));
                 vsorted = kalt ? v1 : v0;
             }
             // ranges of at most KD_CTA members finish in one CTA each
@@ -2800,7 +2826,7 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         RS_LAUNCH(ctx, "rf_lvl_keys", k_lvl_keys, T, TQ, 0, L, nd, uf, (const int *)csize, (const int *)cmin,
                   (unsigned long long *)k0, v0, (int)min_n, ctx->d_status);
         bool alt = false;
-        RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, LM, 32 + rbits, &alt));
+        RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, LM, 32 + rbits, &alt, "sort_child"));
         const unsigned long long *sk = (const unsigned long long *)(alt ? k1 : k0);
         const unsigned *sv = alt ? v1 : v0;
         unsigned *dest = (unsigned *)(alt ? v0 : v1);

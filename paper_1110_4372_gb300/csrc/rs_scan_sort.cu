@@ -229,8 +229,10 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) k_sort_scatter(const K *kin, 
 }
 
 template <typename K>
-rs_status radix_sort(rs_ctx *ctx, K *k0, K *k1, uint32_t *v0, uint32_t *v1, int64_t n, int nbits, bool *alt)
+rs_status radix_sort(rs_ctx *ctx, K *k0, K *k1, uint32_t *v0, uint32_t *v1, int64_t n, int nbits, bool *alt,
+                     const char *tag)
 {
+    const std::string hist_name = std::string(tag) + "_hist", scatter_name = std::string(tag) + "_scatter";
     *alt = false;
     if (n <= 1 || nbits <= 0) return RS_OK;
     if (n >= ((int64_t)1 << 32)) return rs_fail(ctx, RS_ERR_TOO_LARGE, "radix sort of 2^32 or more keys");
@@ -239,9 +241,9 @@ rs_status radix_sort(rs_ctx *ctx, K *k0, K *k1, uint32_t *v0, uint32_t *v1, int6
     K *ki = k0, *ko = k1;
     uint32_t *vi = v0, *vo = v1;
     for (int shift = 0; shift < nbits; shift += RADIX_BITS) {
-        RS_LAUNCH(ctx, "sort_hist", k_sort_hist<K>, ntiles, SORT_THREADS, 0, (const K *)ki, n, shift, hist, ntiles);
+        RS_LAUNCH(ctx, hist_name.c_str(), k_sort_hist<K>, ntiles, SORT_THREADS, 0, (const K *)ki, n, shift, hist, ntiles);
         RS_TRY(scan_top<uint32_t>(ctx, hist, (int64_t)RADIX * ntiles, nullptr));
-        RS_LAUNCH(ctx, "sort_scatter", k_sort_scatter<K>, ntiles, SORT_THREADS, 0, (const K *)ki, ko,
+        RS_LAUNCH(ctx, scatter_name.c_str(), k_sort_scatter<K>, ntiles, SORT_THREADS, 0, (const K *)ki, ko,
                   (const uint32_t *)vi, vo, n, shift, (const uint32_t *)hist, ntiles);
         K *tk = ki;
         ki = ko;
@@ -267,14 +269,14 @@ rs_status rs_scan_i64(rs_ctx *ctx, int64_t *data, int64_t n, int64_t *total)
 }
 
 rs_status rs_radix_sort_u64(rs_ctx *ctx, uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, int64_t n,
-                            int nbits, bool *alt)
+                            int nbits, bool *alt, const char *tag)
 {
     return radix_sort<unsigned long long>(ctx, (unsigned long long *)k0, (unsigned long long *)k1, v0, v1, n,
-                                          nbits, alt);
+                                          nbits, alt, tag);
 }
 
 rs_status rs_radix_sort_u32(rs_ctx *ctx, uint32_t *k0, uint32_t *k1, uint32_t *v0, uint32_t *v1, int64_t n,
-                            int nbits, bool *alt)
+                            int nbits, bool *alt, const char *tag)
 {
-    return radix_sort<uint32_t>(ctx, k0, k1, v0, v1, n, nbits, alt);
+    return radix_sort<uint32_t>(ctx, k0, k1, v0, v1, n, nbits, alt, tag);
 }

@@ -472,6 +472,18 @@ def rs_set_tuning(ctx: Context, **fields) -> dict:
     return t.as_dict()
 
 
+TUNING_FILE = os.path.join(_HERE, "tuning_gb300.json")
+
+
+def apply_tuning(ctx: Context, path: str = TUNING_FILE) -> dict:
+    """Applies the "tuned" table of a tuner record (tune.py --out; by default
+    the record of the GB300 run shipped with the package, whose table the
+    library's defaults already equal) to the context."""
+    import json
+    with open(path) as fh:
+        return rs_set_tuning(ctx, **json.load(fh)["tuned"])
+
+
 def rs_workspace_bytes(ctx: Context) -> int:
     return int(lib().rs_workspace_bytes(ctx.handle))
 
