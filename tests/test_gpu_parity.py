@@ -462,3 +462,19 @@ def test_bracket_fallback_redoes_only_failed_nodes_exactly(rs, monkeypatch):
     monkeypatch.delenv("RS_FAULT")
     _, _, st = rs.rs_find_halos(ctx2, p, v, cat.box)
     assert st["n_fallback_levels"] == 0
+
+
+@pytest.mark.parametrize("n,pinned", [(4001, True), (4002, False), (4003, True)])
+def test_find_halos_host_buffers_odd_sizes(rs, ctx, n, pinned):
+    """Host-buffer calls copy pinned positions with a kernel (16-byte words
+    and a 4-byte tail, here n % 4 != 0) and pageable ones with a plain copy;
+    both give the oracle's halo ids and labels."""
+    c = synth.generate("c1", seed=n, n=n, box=10.0 * (n / 32768) ** (1 / 3), n_halos=12)
+    o = run_oracle_path(c)
+    hp, hv = torch.from_numpy(c.pos), torch.from_numpy(c.vel)
+    lab = torch.full((c.n,), -3, dtype=torch.int32)
+    if pinned:
+        hp, hv, lab = hp.pin_memory(), hv.pin_memory(), lab.pin_memory()
+    hid, _, _ = rs.rs_find_halos(ctx, hp, hv, c.box, fof_labels=lab)
+    assert np.array_equal(hid.numpy(), o["halo_id"])
+    assert np.array_equal(lab.numpy(), o["labels"])
