@@ -1517,8 +1517,11 @@ __device__ __forceinline__ bool link_child(const BvhView &V, int ent, int lane, 
     if (!(c < V.cnt[ch] && !(ch == 0 && c == own) && bvh_m0(ch, c + 1) > (int64_t)q + 1)) return false;
     const int64_t bi = V.off[ch] + c;
     const Box6 bx = box_get(V.S, bi);
+    // the clique flag is loaded with the box, not after the reach test, so
+    // its latency overlaps the box loads instead of following them
+    const unsigned char clique = V.S.cl[bi];
     if (!(point_box_d2(pq, vq, bx, met) <= lm.lim)) return false;
-    if (V.S.cl[bi] && point_box_far2(pq, vq, bx, met) <= lm.cl_lim) {
+    if (clique && point_box_far2(pq, vq, bx, met) <= lm.cl_lim) {
         join_friend(parent, first + q, first + (int)bvh_m0(ch, c), rq, st);
         return false;
     }
@@ -1835,7 +1838,7 @@ __device__ __forceinline__ unsigned kd_coord(const float4 *wpos, const float4 *w
 // sorted by the round's axis; smaller ranges keep their order (value 0).
 __global__ void k_kd_keys(LevelBufs L, NodeArrays nd, const int64_t *seg_base, const float4 *wpos,
                           const float4 *wvel, const unsigned *vin, unsigned long long *kout, unsigned *vout,
-                          int round)
+                          int round, int key32)
 {
     const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x];
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
@@ -1859,8 +1862,27 @@ __global__ void k_kd_keys(LevelBufs L, NodeArrays nd, const int64_t *seg_base, c
         const float iv = nd.sigv[node] > 0 ? (float)(1.0 / nd.sigv[node]) : 0.f;
         qv = kd_coord(wpos, wvel, slot, round % 6, L.ref[2 * k], L.ref[2 * k + 1], ix, iv);
     }
-    kout[P] = ((unsigned long long)(seg_base[k] + start / 32) << 16) | qv;
+    // Key: (block of KD_CTA members holding the range's start, coordinate).
+    // A range still being split has more than KD_CTA members, so it is the
+    // only such range whose start lies in its block, and a later range starts
+    // in a later block; ranges already final (coordinate 0) that share the
+    // block lie before it and keep their places under the stable sort.  So
+    // the block number separates what must stay apart, with 5 fewer bits
+    // than a leaf number.
+    const unsigned long long key = ((unsigned long long)(seg_base[k] + start / KD_CTA) << 16) | qv;
+    if (key32)
+        ((unsigned *)kout)[P] = (unsigned)key;
+    else
+        kout[P] = key;
     vout[P] = slot;
+}
+
+// blocks of KD_CTA members per node (the range keys of the k-d rounds)
+__global__ void k_kd_blocks(const int *list, int K, NodeArrays nd, int64_t *nb)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    nb[k] = ceil_div(nd.count[list[k]], KD_CTA);
 }
 
 // Ranges of at most KD_CTA members left by the global rounds, one entry per
@@ -2640,21 +2662,26 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
             RS_TRY(rs_read_i64(ctx, tot + 3, 1, &maxn, "rs_refine6d"));
             RS_WS(ctx, int64_t, kw, WS_RF_MISC5, 2 * (K + 1) + 8);
             int64_t *kseg = kw, *ktot = kw + (K + 1);
-            RS_LAUNCH(ctx, "rf_full_prep", k_full_prep, ceil_div(K, 256), 256, 0, (const int *)cur, (int)K, nd, kseg,
-                      0);
+            RS_LAUNCH(ctx, "rf_kd_blocks", k_kd_blocks, ceil_div(K, 256), 256, 0, (const int *)cur, (int)K, nd, kseg);
             RS_CUDA(ctx, cudaMemsetAsync(kseg + K, 0, sizeof(int64_t), ctx->stream));
             RS_TRY(rs_scan_i64(ctx, kseg, K + 1, ktot));
             int64_t NS;
             RS_TRY(rs_read_i64(ctx, ktot, 1, &NS, "rs_refine6d"));
             int sbits = 0;
             while (sbits < 40 && (NS >> sbits) != 0) sbits++;
+            // 32-bit keys (half the bytes, four passes) while the blocks fit in 16 bits
+            const int key32 = 16 + sbits <= 32 ? 1 : 0;
             const int R = kd_rounds(maxn, KD_CTA);
             const unsigned *vsorted = nullptr;
             for (int r = 0; r < R; r++) {
                 RS_LAUNCH(ctx, "rf_kd_keys", k_kd_keys, T, TQ, 0, L, nd, (const int64_t *)kseg, (const float4 *)wpos,
-                          (const float4 *)wvel, vsorted, (unsigned long long *)k0, v0, r);
+                          (const float4 *)wvel, vsorted, (unsigned long long *)k0, v0, r, key32);
                 bool kalt = false;
-                RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, LM, 16 + sbits, &kalt, "sort_kd"));
+                if (key32)
+                    RS_TRY(rs_radix_sort_u32(ctx, (uint32_t *)k0, (uint32_t *)k1, v0, v1, LM, 16 + sbits, &kalt,
+                                             "sort_kd"));
+                else
+                    RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, LM, 16 + sbits, &kalt, "sort_kd"));
                 vsorted = kalt ? v1 : v0;
             }
             // ranges of at most KD_CTA members finish in one CTA each
@@ -2666,7 +2693,8 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
                       ctx->d_status);
             if (R == 0)  // every member in its own position: round 0 writes the slots
                 RS_LAUNCH(ctx, "rf_kd_keys", k_kd_keys, T, TQ, 0, L, nd, (const int64_t *)kseg,
-                          (const float4 *)wpos, (const float4 *)wvel, vsorted, (unsigned long long *)k0, v0, 0);
+                          (const float4 *)wpos, (const float4 *)wvel, vsorted, (unsigned long long *)k0, v0, 0,
+                          key32);
             unsigned *vfin = R > 0 ? (unsigned *)vsorted : v0;
             RS_LAUNCH(ctx, "rf_kd_finish", k_kd_finish, (int64_t)ctx->num_sms * 8, 256, 0, L, nd,
                       (const int4 *)kranges, (const int *)kcount, (const float4 *)wpos, (const float4 *)wvel, vfin);
