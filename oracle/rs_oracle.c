@@ -488,8 +488,8 @@ static int moments_of(const float *pos, const float *vel, const int32_t *mem, in
     for (int64_t a = 0; a < n; a++) {
         int32_t i = mem[a];
         for (int d = 0; d < 3; d++) {
-            double dx = min_image((double)pos[3 * i + d] - (double)pos[3 * ref + d], box);
-            double dv = (double)vel[3 * i + d] - (double)vel[3 * ref + d];
+            double dx = min_image((double)pos[3 * (int64_t)i + d] - (double)pos[3 * (int64_t)ref + d], box);
+            double dv = (double)vel[3 * (int64_t)i + d] - (double)vel[3 * (int64_t)ref + d];
             ks_add(&sx[d], dx);
             ks_add(&sv[d], dv);
             if (dx < lo[d]) lo[d] = dx;
@@ -507,19 +507,19 @@ static int moments_of(const float *pos, const float *vel, const int32_t *mem, in
     for (int64_t a = 0; a < n; a++) {
         int32_t i = mem[a];
         for (int d = 0; d < 3; d++) {
-            double dx = min_image((double)pos[3 * i + d] - (double)pos[3 * ref + d], box) - mx[d];
-            double dv = ((double)vel[3 * i + d] - (double)vel[3 * ref + d]) - mv[d];
+            double dx = min_image((double)pos[3 * (int64_t)i + d] - (double)pos[3 * (int64_t)ref + d], box) - mx[d];
+            double dv = ((double)vel[3 * (int64_t)i + d] - (double)vel[3 * (int64_t)ref + d]) - mv[d];
             ks_add(&qx, dx * dx);
             ks_add(&qv, dv * dv);
         }
     }
     for (int d = 0; d < 3; d++) {
-        double x = (double)pos[3 * ref + d] + mx[d];
+        double x = (double)pos[3 * (int64_t)ref + d] + mx[d];
         x = fmod(x, box);
         if (x < 0) x += box;
         if (x >= box) x -= box;
         m->xbar[d] = x;
-        m->vbar[d] = (double)vel[3 * ref + d] + mv[d];
+        m->vbar[d] = (double)vel[3 * (int64_t)ref + d] + mv[d];
     }
     m->sigx = sqrt(ks_val(&qx) / (double)n);
     m->sigv = sqrt(ks_val(&qv) / (double)n);
@@ -534,8 +534,8 @@ static double dist2_6d(const float *pos, const float *vel, int32_t i, int32_t j,
 {
     double sx = 0.0, sv = 0.0;
     for (int d = 0; d < 3; d++) {
-        double dx = min_image((double)pos[3 * i + d] - (double)pos[3 * j + d], box);
-        double dv = (double)vel[3 * i + d] - (double)vel[3 * j + d];
+        double dx = min_image((double)pos[3 * (int64_t)i + d] - (double)pos[3 * (int64_t)j + d], box);
+        double dv = (double)vel[3 * (int64_t)i + d] - (double)vel[3 * (int64_t)j + d];
         sx += dx * dx;
         sv += dv * dv;
     }
@@ -874,8 +874,8 @@ static int refine_node(or_tree *t, int64_t id)
         if (!u) return OR_ERR_OOM;
         for (int64_t a = 0; a < n; a++) {
             for (int d = 0; d < 3; d++) {
-                double dx = min_image((double)t->pos[3 * mem[a] + d] - (double)t->pos[3 * ref + d], t->box);
-                double dv = (double)t->vel[3 * mem[a] + d] - (double)t->vel[3 * ref + d];
+                double dx = min_image((double)t->pos[3 * (int64_t)mem[a] + d] - (double)t->pos[3 * (int64_t)ref + d], t->box);
+                double dv = (double)t->vel[3 * (int64_t)mem[a] + d] - (double)t->vel[3 * (int64_t)ref + d];
                 u[6 * a + d] = m.sigx > 0 ? dx / m.sigx : 0.0;
                 u[6 * a + 3 + d] = m.sigv > 0 ? dv / m.sigv : 0.0;
             }
@@ -1214,7 +1214,7 @@ double rdyn2_of(const float *pos, const int32_t *mem, int64_t n, double box, con
     for (int64_t p = 0; p < n; p++) {
         double s = 0;
         for (int d = 0; d < 3; d++) {
-            double dx = min_image((double)pos[3 * mem[p] + d] - xbar[d], box);
+            double dx = min_image((double)pos[3 * (int64_t)mem[p] + d] - xbar[d], box);
             s += dx * dx;
         }
         r[p] = sqrt(s);
@@ -1427,8 +1427,8 @@ int or_assign(or_tree *t, double delta_vir, double nbar, double merge_thresh, in
                 int32_t h = cand[c];
                 double dx2 = 0, dv2 = 0;
                 for (int d = 0; d < 3; d++) {
-                    double dx = min_image(t->h_xbar[3 * h + d] - (double)pos[3 * pi + d], box);
-                    double dv = t->h_vbar[3 * h + d] - (double)vel[3 * pi + d];
+                    double dx = min_image(t->h_xbar[3 * h + d] - (double)pos[3 * (int64_t)pi + d], box);
+                    double dv = t->h_vbar[3 * h + d] - (double)vel[3 * (int64_t)pi + d];
                     dx2 += dx * dx;
                     dv2 += dv * dv;
                 }
@@ -1613,7 +1613,7 @@ int64_t or_unbind_set(const float *pos, const float *vel, double box, const int3
     const double eps2 = eps * eps;
     ksum sv[3] = {{0, 0}, {0, 0}, {0, 0}};
     for (int64_t a = 0; a < n; a++)
-        for (int d = 0; d < 3; d++) ks_add(&sv[d], (double)vel[3 * mem[a] + d]);
+        for (int d = 0; d < 3; d++) ks_add(&sv[d], (double)vel[3 * (int64_t)mem[a] + d]);
     for (int d = 0; d < 3; d++) vb[d] = n > 0 ? ks_val(&sv[d]) / (double)n : 0.0;
     int64_t nb = 0;
     for (int64_t a = 0; a < n; a++) {
@@ -1624,7 +1624,7 @@ int64_t or_unbind_set(const float *pos, const float *vel, double box, const int3
             const int32_t j = mem[b];
             double r2 = 0;
             for (int d = 0; d < 3; d++) {
-                const double dx = min_image((double)pos[3 * j + d] - (double)pos[3 * i + d], box);
+                const double dx = min_image((double)pos[3 * (int64_t)j + d] - (double)pos[3 * (int64_t)i + d], box);
                 r2 += dx * dx;
             }
             r2 += eps2;
@@ -1632,7 +1632,7 @@ int64_t or_unbind_set(const float *pos, const float *vel, double box, const int3
         }
         double ke = 0;
         for (int d = 0; d < 3; d++) {
-            const double dv = (double)vel[3 * i + d] - vb[d];
+            const double dv = (double)vel[3 * (int64_t)i + d] - vb[d];
             ke += dv * dv;
         }
         if (phi_out) phi_out[a] = ks_val(&phi);
