@@ -3,40 +3,62 @@
 
 #include "rs_refine.cuh"
 
-// Copies `bytes` (a multiple of 4) from a host buffer the device can read in
-// place (mapped pinned memory) into device memory: 16-byte words for the
-// bulk, 4-byte words for the tail.  Used for the positions of a host-buffer
-// call: after the refinement's kernels a copy-engine transfer of a large
-// pinned buffer runs at about 25 GB/s for its first gigabytes on GB300,
-// while this many-SM copy keeps about 200 GB/s.
-__global__ void k_h2d_copy(const float4 *__restrict__ src, float4 *__restrict__ dst, int64_t n16,
-                           const unsigned *__restrict__ src_tail, unsigned *__restrict__ dst_tail, int tail4)
+// Copies `bytes` (a multiple of 4) between device memory and a host buffer
+// the device can address in place (mapped pinned memory): 16-byte words for
+// the bulk, 4-byte words for the tail.  Used for the positions and the halo
+// ids of a host-buffer call: after the refinement's kernels a copy-engine
+// transfer of a large pinned buffer runs at about 15-30 GB/s for its first
+// gigabytes on GB300, while this many-SM copy keeps about 200 GB/s.  The
+// same holds for the velocities, which the second stream copies while the 3D
+// FOF runs.
+__global__ void k_mapped_copy(const float4 *__restrict__ src, float4 *__restrict__ dst, int64_t n16,
+                              const unsigned *__restrict__ src_tail, unsigned *__restrict__ dst_tail, int tail4)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) dst[i] = src[i];
     if (blockIdx.x == 0 && (int)threadIdx.x < tail4) dst_tail[threadIdx.x] = src_tail[threadIdx.x];
 }
 
-// Host-to-device copy of the positions on the context's stream: the copy
-// kernel when the host buffer is mapped pinned memory and both ends are
-// 16-byte aligned, else cudaMemcpyAsync.
-static rs_status copy_in(rs_ctx *ctx, void *dst, const void *src, size_t bytes)
+// The device address of a mapped pinned host buffer, or nullptr.
+static const void *mapped_address(const void *host)
 {
     cudaPointerAttributes a{};
-    const bool mapped = cudaPointerGetAttributes(&a, src) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+    const bool mapped = cudaPointerGetAttributes(&a, host) == cudaSuccess && a.type == cudaMemoryTypeHost &&
                         a.devicePointer != nullptr;
     cudaGetLastError();  // an unregistered pointer may leave an error behind
-    if (mapped && ((uintptr_t)a.devicePointer & 15) == 0 && ((uintptr_t)dst & 15) == 0 && bytes % 4 == 0) {
+    return mapped ? a.devicePointer : nullptr;
+}
+
+// Copy on `stream` between a host buffer and device memory (to_device says
+// which way): the copy kernel (blocks_per_sm CTAs per SM) when the host
+// buffer is mapped pinned memory and both ends are 16-byte aligned, else
+// cudaMemcpyAsync.  (The launch is counted and, when profiling is on, timed
+// like the library's other kernels; the events it records go on the
+// context's stream, so it is timed only there.)
+static rs_status copy_host(rs_ctx *ctx, void *dst, const void *src, size_t bytes, bool to_device,
+                           cudaStream_t stream, int blocks_per_sm, const char *name)
+{
+    const void *host = to_device ? src : (const void *)dst;
+    const char *hdev = (const char *)mapped_address(host);
+    const char *s = to_device ? hdev : (const char *)src;
+    char *d = to_device ? (char *)dst : (char *)hdev;
+    if (hdev && ((uintptr_t)s & 15) == 0 && ((uintptr_t)d & 15) == 0 && bytes % 4 == 0) {
         const int64_t n16 = (int64_t)(bytes / 16);
         const int tail4 = (int)((bytes % 16) / 4);
-        const char *s = (const char *)a.devicePointer;
-        char *d = (char *)dst;
-        const int64_t grid = std::min<int64_t>(std::max<int64_t>(ceil_div(n16, 256), 1), (int64_t)ctx->num_sms * 8);
-        RS_LAUNCH(ctx, "io_h2d_kernel", k_h2d_copy, grid, 256, 0, (const float4 *)s, (float4 *)d, n16,
-                  (const unsigned *)(s + 16 * n16), (unsigned *)(d + 16 * n16), tail4);
+        const int64_t grid =
+            std::min<int64_t>(std::max<int64_t>(ceil_div(n16, 256), 1), (int64_t)ctx->num_sms * blocks_per_sm);
+        const int pr = stream == ctx->stream ? rs_prof_begin(ctx, name) : -1;
+        k_mapped_copy<<<(unsigned)grid, 256, 0, stream>>>((const float4 *)s, (float4 *)d, n16,
+                                                          (const unsigned *)(s + 16 * n16),
+                                                          (unsigned *)(d + 16 * n16), tail4);
+        ctx->launches++;
+        rs_prof_end(ctx, pr);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return rs_cuda_fail(ctx, e, name);
         return RS_OK;
     }
-    RS_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    RS_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost,
+                                 stream));
     return RS_OK;
 }
 
@@ -80,13 +102,14 @@ static rs_status find_halos(rs_ctx *ctx, const float *pos, const float *vel, int
         ev_lab = ctx->ev_io[1];
         ev_lab_done = ctx->ev_io[2];
         const int pr = rs_prof_begin(ctx, "io_h2d_pos");
-        RS_TRY(copy_in(ctx, p, pos, in_bytes));
+        RS_TRY(copy_host(ctx, p, pos, in_bytes, true, ctx->stream, 8, "io_h2d_kernel"));
         rs_prof_end(ctx, pr);
         // the second stream starts after everything already on the context's
         // stream (nothing may still read the velocity workspace)
         RS_CUDA(ctx, cudaEventRecord(ev_lab, ctx->stream));
         RS_CUDA(ctx, cudaStreamWaitEvent(ctx->aux, ev_lab, 0));
-        RS_CUDA(ctx, cudaMemcpyAsync(v, vel, in_bytes, cudaMemcpyHostToDevice, ctx->aux));
+        // the velocities with a narrower copy kernel beside the 3D FOF's
+        RS_TRY(copy_host(ctx, v, vel, in_bytes, true, ctx->aux, 2, "io_h2d_vel_kernel"));
         RS_CUDA(ctx, cudaEventRecord(ev_vel, ctx->aux));
         dpos = p;
         dvel = v;
@@ -141,10 +164,12 @@ static rs_status find_halos(rs_ctx *ctx, const float *pos, const float *vel, int
         }
         if (host_buffers) {
             const int pr = rs_prof_begin(ctx, "io_d2h_halo");
-            cudaError_t e = cudaMemcpyAsync(halo_id, hid, ob, cudaMemcpyDeviceToHost, ctx->stream);
+            s = copy_host(ctx, halo_id, hid, ob, false, ctx->stream, 8, "io_d2h_kernel");
             rs_prof_end(ctx, pr);
-            if (e == cudaSuccess && fof_labels) e = cudaStreamWaitEvent(ctx->stream, ev_lab_done, 0);
-            if (e != cudaSuccess) s = rs_cuda_fail(ctx, e, "rs_find_halos: copy out");
+            if (s == RS_OK && fof_labels) {
+                const cudaError_t e = cudaStreamWaitEvent(ctx->stream, ev_lab_done, 0);
+                if (e != cudaSuccess) s = rs_cuda_fail(ctx, e, "rs_find_halos: copy out");
+            }
         } else if (fof_labels) {
             cudaError_t e = cudaMemcpyAsync(fof_labels, labels, ob, cudaMemcpyDeviceToDevice, ctx->stream);
             if (e != cudaSuccess) s = rs_cuda_fail(ctx, e, "rs_find_halos: copy labels");
@@ -165,6 +190,7 @@ extern "C" rs_status rs_find_halos(rs_ctx *ctx, const float *pos, const float *v
     if (n >= ((int64_t)1 << 31)) return rs_fail(ctx, RS_ERR_TOO_LARGE, "rs_find_halos: n >= 2^31");
     if (stats) *stats = rs_stats{};
     if (n == 0) return RS_OK;
+    RsRange range(host_buffers ? "rs_find_halos (host buffers)" : "rs_find_halos");
     const rs_status s = find_halos(ctx, pos, vel, stride, n, box, params, fof_labels, halo_id, stats, host_buffers);
     return host_buffers ? rs_io_drain(ctx, s) : s;
 }

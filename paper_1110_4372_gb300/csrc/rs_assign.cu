@@ -705,6 +705,7 @@ extern "C" rs_status rs_assign_ex(rs_ctx *ctx, const rs_tree *t, const float *po
                                   rs_halos **halos_out)
 {
     if (!ctx) return RS_ERR_INVALID_ARG;
+    RsRange range("rs_assign");
     if (halos_out) *halos_out = nullptr;
     if (!t || !params || n < 0 || (stride != 3 && stride != 4) || !(box > 0) || (n > 0 && (!pos || !vel || !halo_id)))
         return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_assign: bad argument");

@@ -209,8 +209,10 @@ __device__ __forceinline__ int nth_bit64(uint64_t m, int j)
 // per axis that has a friend pair with it.  Pass 0 takes the 26 adjacent
 // cells (offsets of at most 1 per axis), where pairs are friends almost at
 // once in dense regions; pass 1 takes the cells two apart on some axis, by
-// which time dense regions are mostly one set and the same-set check skips
-// them.  Coarse cells numbered below A's hold only fine cells of smaller
+// which time dense regions are mostly one set: a coarse cell whose fine cells
+// all had one root after pass 0 (uroot at its first fine cell, else -1) is
+// skipped whole when that root is A's, and the same-set check skips the
+// rest.  Coarse cells numbered below A's hold only fine cells of smaller
 // index and are not visited.
 //
 // A warp takes 32 consecutive fine cells, a lane each.  For each of the
@@ -221,7 +223,7 @@ __device__ __forceinline__ int nth_bit64(uint64_t m, int j)
 __global__ void __launch_bounds__(FOF_THREADS, 6) k_fof_link(const uint32_t *n_cells_p, const uint64_t *cell_key,
                                                             const uint32_t *cell_start, const uint32_t *table,
                                                             const uint64_t *occ, const float4 *spos, int *parent,
-                                                            FofGeom g, int pass, rs_dev_status *st)
+                                                            const int *uroot, FofGeom g, int pass, rs_dev_status *st)
 {
     const unsigned FULL = 0xffffffffu;
     const int64_t M = *n_cells_p;
@@ -246,6 +248,9 @@ __global__ void __launch_bounds__(FOF_THREADS, 6) k_fof_link(const uint32_t *n_c
         }
         const int ax = 4 * ccx + ux, ay = 4 * ccy + uy, az = 4 * ccz + uz;
         const int lox = ux < 2 ? -1 : 0, loy = uy < 2 ? -1 : 0, loz = uz < 2 ? -1 : 0;
+        // a root of A's set (sets only grow, so a coarse cell whose common
+        // root equals it is in A's set for the rest of the pass)
+        const int ra = (va && uroot) ? uf_find(parent, (int)A, st) : -1;
         for (int s8 = 0; s8 < 8; s8++) {
             const int dz = loz + (s8 >> 2), dy = loy + ((s8 >> 1) & 1), dx = lox + (s8 & 1);
             int cz = ccz + dz, cy = ccy + dy, cx = ccx + dx;
@@ -258,7 +263,7 @@ __global__ void __launch_bounds__(FOF_THREADS, 6) k_fof_link(const uint32_t *n_c
                 const uint64_t cc = ((uint64_t)cz * g.Gc + cy) * g.Gc + cx;
                 if (cc >= ca) {  // coarse cells below A's hold only fine cells of smaller index
                     b0c = table[cc];
-                    if (b0c != 0xffffffffu) {
+                    if (b0c != 0xffffffffu && !(ra >= 0 && uroot[b0c] == ra)) {
                         om = occ[b0c];
                         const uint64_t near = reach_mask(ux, uy, uz, dx, dy, dz, 1);
                         cand = om & (pass == 0 ? near : reach_mask(ux, uy, uz, dx, dy, dz, 2) & ~near);
@@ -322,6 +327,27 @@ __global__ void __launch_bounds__(FOF_THREADS, 6) k_fof_link(const uint32_t *n_c
                 for (int u = 0; u < used; u++) cand &= cand - 1ull;
             }
         }
+    }
+}
+
+// the root of every coarse cell's first fine cell, kept at that cell
+__global__ void k_fof_uroot_first(const uint32_t *n_cells_p, const uint64_t *cell_key, const uint32_t *table,
+                                  int *parent, int *uroot, rs_dev_status *st)
+{
+    const int64_t M = *n_cells_p;
+    for (int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; A < M; A += (int64_t)gridDim.x * blockDim.x)
+        if (table[cell_key[A] >> 6] == (uint32_t)A) uroot[A] = uf_find(parent, (int)A, st);
+}
+
+// -1 at the first fine cell of every coarse cell whose fine cells do not all
+// share that root (no unions run meanwhile, so roots are fixed)
+__global__ void k_fof_uroot_check(const uint32_t *n_cells_p, const uint64_t *cell_key, const uint32_t *table,
+                                  int *parent, int *uroot, rs_dev_status *st)
+{
+    const int64_t M = *n_cells_p;
+    for (int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; A < M; A += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t b0 = table[cell_key[A] >> 6];
+        if (b0 != (uint32_t)A && uf_find(parent, (int)A, st) != uroot[b0]) uroot[b0] = -1;
     }
 }
 
@@ -641,6 +667,7 @@ rs_status fof_run(rs_ctx *ctx, const float *pos, int32_t stride, int64_t n, doub
         return RS_OK;
     }
     RsStageGuard running(&ctx->in_fof);
+    RsRange range(dense_n >= 0 ? "rs_fof3d_accel" : "rs_fof3d");
     FofGeom g;
     RS_TRY(fof_geometry(ctx, n, box, b, &g));
     const int64_t T = FOF_THREADS;
@@ -685,10 +712,20 @@ rs_status fof_run(rs_ctx *ctx, const float *pos, int32_t stride, int64_t n, doub
     RS_LAUNCH(ctx, "fof_iota", k_iota_i32, nb, T, 0, parent, n);
     RS_LAUNCH(ctx, "fof_fill", k_fill_u32, std::min<int64_t>(nb, (int64_t)ctx->num_sms * 16), T, 0,
               (uint32_t *)root_min, n, 0x7fffffffu);
-    for (int pass = 0; pass < 2; pass++)
+    // (flag's first n words are free once the cells are numbered: they hold
+    // the common root of each coarse cell between the passes)
+    int *uroot = (int *)flag;
+    for (int pass = 0; pass < 2; pass++) {
+        if (pass == 1) {
+            RS_LAUNCH(ctx, "fof_uroot_first", k_fof_uroot_first, grid, T, 0, (const uint32_t *)n_cells,
+                      (const uint64_t *)cell_key, (const uint32_t *)table, parent, uroot, ctx->d_status);
+            RS_LAUNCH(ctx, "fof_uroot_check", k_fof_uroot_check, grid, T, 0, (const uint32_t *)n_cells,
+                      (const uint64_t *)cell_key, (const uint32_t *)table, parent, uroot, ctx->d_status);
+        }
         RS_LAUNCH(ctx, "fof_link", k_fof_link, grid, T, 0, (const uint32_t *)n_cells, (const uint64_t *)cell_key,
                   (const uint32_t *)cell_start, (const uint32_t *)table, (const uint64_t *)occ, (const float4 *)spos,
-                  parent, g, pass, ctx->d_status);
+                  parent, pass == 1 ? (const int *)uroot : nullptr, g, pass, ctx->d_status);
+    }
     if (dense_n >= 0) {
         // accelerated variant: dense flags, centre rounds, 2l joins
         RS_WS(ctx, uint8_t, acc, WS_FOF_ACC, 2 * n + 64);
@@ -765,16 +802,23 @@ extern "C" rs_status rs_fof3d_accel(rs_ctx *ctx, const float *pos, int32_t strid
 // ---------------------------------------------------------------------------
 namespace {
 
+// Members per label.  The lanes of a warp that share a label add together
+// (one atomic per distinct label in the warp): neighbours in the input often
+// belong to one group, whose counter would otherwise take one atomic per
+// member.
 __global__ void k_gs_count(int64_t n, const int32_t *labels, uint32_t *count, rs_dev_status *st)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int32_t l = labels[i];
-    if (l < 0 || l > i) {
-        dev_fail(st, DEV_BADARG, 20, i);
-        return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t l = -1;
+    if (i < n) {
+        l = labels[i];
+        if (l < 0 || l > i) {
+            dev_fail(st, DEV_BADARG, 20, i);
+            l = -1;
+        }
     }
-    atomicAdd(&count[l], 1u);
+    const unsigned peers = __match_any_sync(0xffffffffu, l);
+    if (l >= 0 && lane_id() == __ffs(peers) - 1) atomicAdd(&count[l], (uint32_t)__popc(peers));
 }
 
 // root flags: groups of >= min_n members, keyed by their label (= root index)
@@ -831,6 +875,7 @@ extern "C" rs_status rs_group_sort(rs_ctx *ctx, const int32_t *labels, int64_t n
         return RS_OK;
     }
     RsStageGuard running(&ctx->in_gs);
+    RsRange range("rs_group_sort");
     const int64_t T = 256, nb = ceil_div(n, T);
     RS_WS(ctx, uint32_t, count, WS_GS_COUNT, n);
     RS_WS(ctx, uint32_t, fl, WS_GS_FLAG, 4 * n + 8);

@@ -751,6 +751,7 @@ extern "C" rs_status rs_halo_props(rs_ctx *ctx, const rs_tree *t, const rs_halos
                                    int32_t *host)
 {
     if (!ctx) return RS_ERR_INVALID_ARG;
+    RsRange range("rs_halo_props");
     if (!t || !hs || n != t->n_total || hs->n_nodes != t->n_nodes || (n > 0 && !halo_id))
         return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_halo_props: bad argument");
     const int64_t H = hs->n_halos;
@@ -785,6 +786,7 @@ extern "C" rs_status rs_unbind(rs_ctx *ctx, const rs_tree *t, const rs_halos *hs
                                double gm, double eps, double theta, int64_t *n_part, int64_t *n_bound,
                                double *vbulk, int8_t *bound_own, double *phi_own)
 {
+    RsRange range("rs_unbind");
     if (!ctx) return RS_ERR_INVALID_ARG;
     if (!t || !hs || n != t->n_total || (stride != 3 && stride != 4) || !(gm >= 0) || !(eps >= 0) ||
         !(theta >= 0 && theta < 1) || (n > 0 && (!halo_id || !pos || !vel || !bound_own)))

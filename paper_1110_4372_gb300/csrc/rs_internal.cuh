@@ -10,7 +10,17 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rsgpu.h"
+
+// NVTX range over a scope: each entry point and stage is named for a
+// profiler that attaches (ncu --nvtx, Nsight Systems); without one it costs
+// a function-pointer check.
+struct RsRange {
+    explicit RsRange(const char *name) { nvtxRangePushA(name); }
+    ~RsRange() { nvtxRangePop(); }
+};
 
 // ---------------------------------------------------------------------------
 // Device status word: kernels that hit a bounded wait or a capacity limit
@@ -54,7 +64,7 @@ enum rs_ws_slot {
     WS_RF_POS, WS_RF_VEL, WS_RF_POS2, WS_RF_VEL2, WS_RF_IDX2,
     WS_RF_DNN, WS_RF_PARENT, WS_RF_MISC0, WS_RF_MISC1, WS_RF_MISC2, WS_RF_MISC3, WS_RF_NODEQ,
     WS_RF_ACC, WS_RF_HIST, WS_RF_BAND, WS_RF_MISC4, WS_RF_MISC5, WS_RF_JOBS, WS_RF_JOBS2, WS_RF_SDNN, WS_RF_R2,
-    WS_RF_SRCH, WS_RF_SUBQ,
+    WS_RF_SRCH, WS_RF_SUBQ, WS_RF_KDV,
     WS_HL_IDS, WS_HL_PURE, WS_HL_BEST, WS_HL_OFF, WS_HL_TILES, WS_HL_TREE, WS_HL_REF, WS_HL_UPOS, WS_HL_TPOS,
     WS_HL_TMEM, WS_HL_MK0, WS_HL_MK1, WS_HL_MV0, WS_HL_MV1, WS_HL_BOX, WS_HL_JOBS,
     WS_AS_0, WS_AS_1, WS_AS_2, WS_AS_3, WS_AS_4, WS_AS_5, WS_AS_6, WS_AS_7, WS_AS_8, WS_AS_9,

@@ -1245,7 +1245,7 @@ __global__ void __launch_bounds__(256) k_bvh_linkbox(LevelBufs L, NodeArrays nd,
 // the bit patterns, which order like the non-negative floats) updates the
 // radius.  The leaves under an opened box are scanned nearest first and
 // re-tested as the radius shrinks; needed inner boxes are pushed on a
-// shared-memory stack farthest first, each with its bound.
+// shared-memory stack all at once, each with its bound, the nearest on top.
 constexpr int W_WARPS = 8;    // warps per block of the search kernels
 constexpr int W_STACK = 192;  // stack entries per warp: at most 31 pending per level
 constexpr unsigned FULLW = 0xffffffffu;
@@ -1326,17 +1326,28 @@ __device__ __forceinline__ float w32_nn(const BvhView &V, const MemberStore &M, 
             if (lane == 0) dev_fail(st, DEV_OVERFLOW, 54, node);
             return best;
         }
-        while (mask) {
+        if (mask) {
             const bool mine = (mask >> lane) & 1u;
-            const unsigned key = mine ? ford(lb) : 0u;
-            const unsigned mx = __reduce_max_sync(FULLW, key);
-            const int src = __ffs(__ballot_sync(FULLW, mine && key == mx)) - 1;
-            if (lane == src) {
-                si[sp] = (ch << 24) | c;
-                sd[sp] = lb;
+            const int cntm = __popc(mask);
+            if (mine) {
+                const int slot = sp + __popc(mask & ((1u << lane) - 1u));
+                si[slot] = (ch << 24) | c;
+                sd[slot] = lb;
             }
-            sp++;
-            mask &= ~(1u << src);
+            const unsigned key = mine ? ford(lb) : 0xffffffffu;
+            const unsigned mn = __reduce_min_sync(FULLW, key);
+            const int src = __ffs(__ballot_sync(FULLW, mine && key == mn)) - 1;
+            const int top = sp + cntm - 1, from = sp + __popc(mask & ((1u << src) - 1u));
+            __syncwarp();
+            if (lane == 0 && from != top) {
+                const int e0 = si[from];
+                const float d0 = sd[from];
+                si[from] = si[top];
+                sd[from] = sd[top];
+                si[top] = e0;
+                sd[top] = d0;
+            }
+            sp += cntm;
         }
         __syncwarp();
     }
@@ -1345,18 +1356,19 @@ __device__ __forceinline__ float w32_nn(const BvhView &V, const MemberStore &M, 
 
 // nearest-neighbour distances, one warp per job of 32 consecutive members
 // (one leaf): the leaf is held in registers, one member per lane, and its 32
-// queries are searched one after another
+// queries are searched one after another.  Blocks are of NN_WARPS warps, so a
+// slot frees as soon as its few warps end.
+constexpr int NN_WARPS = 4;
 template <int MINB>
-__global__ void __launch_bounds__(W_WARPS * 32, MINB) k_bvh_nn(LevelBufs L, WarpJobs J, NodeArrays nd,
-                                                         const int64_t *box_base, BoxStore B, MemberStore MS,
-                                                         const float *R2, const float *STOP, int redo_failed,
-                                                         float *out, rs_dev_status *st)
+__global__ void __launch_bounds__(NN_WARPS * 32, MINB * W_WARPS / NN_WARPS)
+    k_bvh_nn(LevelBufs L, WarpJobs J, NodeArrays nd, const int64_t *box_base, BoxStore B, MemberStore MS,
+             const float *R2, const float *STOP, int redo_failed, float *out, rs_dev_status *st)
 {
-    __shared__ int si_s[W_WARPS][W_STACK];
-    __shared__ float sd_s[W_WARPS][W_STACK];
-    __shared__ int lv_s[W_WARPS][2 * BVH_MAXH];
+    __shared__ int si_s[NN_WARPS][W_STACK];
+    __shared__ float sd_s[NN_WARPS][W_STACK];
+    __shared__ int lv_s[NN_WARPS][2 * BVH_MAXH];
     const int w = warp_id(), lane = lane_id();
-    const int64_t gw = (int64_t)blockIdx.x * W_WARPS + w;
+    const int64_t gw = (int64_t)blockIdx.x * NN_WARPS + w;
     if (gw >= J.count) return;
     const int k = J.rank[gw], q0 = J.q0[gw];
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
@@ -1616,17 +1628,26 @@ __device__ __forceinline__ int w32_link(const BvhView &V, const MemberStore &M, 
 
 // friends-of-friends at l, one warp per leaf of 32 consecutive members, pairs
 // with the candidate after the query in the node's member order; only
-// members with a neighbour within reach take part
+// members with a neighbour within reach take part.  A tile's eight warps are
+// spread over blocks of LK_WARPS warps: the cost of a leaf varies widely, and
+// a small block frees its slot as soon as its own few warps end instead of
+// waiting for the slowest of eight.
+constexpr int LK_WARPS = 2;
 template <int MINB>
-__global__ void __launch_bounds__(TQ, MINB) k_bvh_link(LevelBufs L, NodeArrays nd, const int64_t *box_base,
-                                                 BoxStore B, MemberStore MS, const float *dnn, int *parent,
-                                                 rs_dev_status *st)
+__global__ void __launch_bounds__(LK_WARPS * 32, MINB * (TQ / 32) / LK_WARPS)
+    k_bvh_link(LevelBufs L, NodeArrays nd, const int64_t *box_base, BoxStore B, MemberStore MS, const float *dnn,
+               int *parent, rs_dev_status *st)
 {
-    __shared__ int si_s[TQ / 32][LK_STACK];
-    __shared__ int lf_s[TQ / 32][LK_LEAVES];
-    __shared__ int lv_s[TQ / 32][2 * BVH_MAXH];
+    static_assert((TQ / 32) % LK_WARPS == 0, "a tile's warps fill whole blocks");
+    __shared__ int si_s[LK_WARPS][LK_STACK];
+    __shared__ int lf_s[LK_WARPS][LK_LEAVES];
+    __shared__ int lv_s[LK_WARPS][2 * BVH_MAXH];
     const int w = warp_id(), lane = lane_id();
-    const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x] + 32 * w;
+    // the grid holds exactly the tiles' warps: block b takes warps
+    // (b % bpt) * LK_WARPS + w of tile b / bpt
+    constexpr int bpt = (TQ / 32) / LK_WARPS;
+    const int tile = blockIdx.x / bpt, jw = (blockIdx.x % bpt) * LK_WARPS + w;
+    const int k = L.tile_rank[tile], q0 = L.tile_q0[tile] + 32 * jw;
     const int node = L.list[k], first = nd.first[node], n = nd.count[node];
     if (q0 >= n) return;
     Metric6 met;  // float32 factors only; the float64 ones are read where needed
@@ -1834,18 +1855,21 @@ __device__ __forceinline__ unsigned kd_coord(const float4 *wpos, const float4 *w
     return (unsigned)fminf(fmaxf(u, 0.f), 65535.f);
 }
 
-// One global round: ranges of more than KD_CTA members at this depth are
-// sorted by the round's axis; smaller ranges keep their order (value 0).
-__global__ void k_kd_keys(LevelBufs L, NodeArrays nd, const int64_t *seg_base, const float4 *wpos,
-                          const float4 *wvel, const unsigned *vin, unsigned long long *kout, unsigned *vout,
-                          int round, int key32)
+// One global round over the nodes still being split (act_off: their members'
+// offsets in the round's compact arrays; equal neighbours mark a node that is
+// done): ranges of more than KD_CTA members at this depth are sorted by the
+// round's axis; smaller ranges keep their order (value 0).  vcur holds every
+// member's slot in the current order.
+__global__ void k_kd_keys(LevelBufs L, NodeArrays nd, const int64_t *seg_base, const int64_t *act_off,
+                          const float4 *wpos, const float4 *wvel, const unsigned *vcur, unsigned long long *kout,
+                          unsigned *vout, int round, int key32)
 {
     const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x];
-    const int node = L.list[k], first = nd.first[node], n = nd.count[node];
+    const int node = L.list[k], n = nd.count[node];
     const int p = q0 + threadIdx.x;
-    if (p >= n) return;
-    const int64_t P = L.seg_off[k] + p;
-    const unsigned slot = round == 0 ? (unsigned)(first + p) : vin[P];
+    if (p >= n || act_off[k + 1] == act_off[k]) return;
+    const int64_t A = act_off[k] + p;
+    const unsigned slot = vcur[L.seg_off[k] + p];
     int start = 0, size = n;
     for (int i = 0; i < round && size > KD_CTA; i++) {
         const int h = kd_split(size);
@@ -1871,18 +1895,42 @@ __global__ void k_kd_keys(LevelBufs L, NodeArrays nd, const int64_t *seg_base, c
     // than a leaf number.
     const unsigned long long key = ((unsigned long long)(seg_base[k] + start / KD_CTA) << 16) | qv;
     if (key32)
-        ((unsigned *)kout)[P] = (unsigned)key;
+        ((unsigned *)kout)[A] = (unsigned)key;
     else
-        kout[P] = key;
-    vout[P] = slot;
+        kout[A] = key;
+    vout[A] = slot;
 }
 
-// blocks of KD_CTA members per node (the range keys of the k-d rounds)
-__global__ void k_kd_blocks(const int *list, int K, NodeArrays nd, int64_t *nb)
+// the round's sorted slots back to their nodes' places in the current order
+__global__ void k_kd_back(LevelBufs L, NodeArrays nd, const int64_t *act_off, const unsigned *vs, unsigned *vcur)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x];
+    const int n = nd.count[L.list[k]];
+    const int p = q0 + threadIdx.x;
+    if (p >= n || act_off[k + 1] == act_off[k]) return;
+    vcur[L.seg_off[k] + p] = vs[act_off[k] + p];
+}
+
+// the current order before the rounds: every member in its own place
+__global__ void k_kd_init(LevelBufs L, NodeArrays nd, unsigned *vcur)
+{
+    const int k = L.tile_rank[blockIdx.x], q0 = L.tile_q0[blockIdx.x];
+    const int node = L.list[k], n = nd.count[node];
+    const int p = q0 + threadIdx.x;
+    if (p < n) vcur[L.seg_off[k] + p] = (unsigned)(nd.first[node] + p);
+}
+
+// Nodes still being split in round r (their largest range at depth r, the
+// first, has more than KD_CTA members): blocks of KD_CTA members (the range
+// keys) and members; 0 for the others, which sit the round out.
+__global__ void k_kd_active(const int *list, int K, NodeArrays nd, int round, int64_t *nb, int64_t *na)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
-    nb[k] = ceil_div(nd.count[list[k]], KD_CTA);
+    const int n = nd.count[list[k]];
+    const bool act = kd_rounds(n, KD_CTA) > round;
+    nb[k] = act ? ceil_div(n, KD_CTA) : 0;
+    na[k] = act ? n : 0;
 }
 
 // Ranges of at most KD_CTA members left by the global rounds, one entry per
@@ -1923,15 +1971,94 @@ __global__ void k_kd_ranges(LevelBufs L, NodeArrays nd, int4 *ranges, int *count
     }
 }
 
-// Finish one range in shared memory: the remaining splits, each round a
-// bitonic sort of (sub-range, coordinate, element) keys.
+// Finish one range in shared memory: the remaining splits.  Round r orders
+// every sub-range of more than 32 members (at depth r) along the round's axis,
+// which puts its leaf-aligned median split in place, as the global rounds do.
+// The members' ranks along each axis the range uses come first, from a
+// stable two-pass radix sort of their 16-bit coordinates (ties keep the
+// order the range came in); a round then moves member e of sub-range s to s's
+// start plus the number of s's members of smaller rank, counted from a
+// bitmap of the ranks per sub-range and its prefix popcounts.
+constexpr int KDF_ROUNDS = 5;   // kd_rounds(KD_CTA, 32)
+constexpr int KDF_SUB = 16;     // sub-ranges ordered in the last round
+static_assert(KD_CTA == 8 * 128, "eight warps of 128 positions rank a range");
+
+// stable radix ranking of key[0..m) (16-bit): rk[e] = position of element e
+// in the sorted order (8 warps, positions 128 w .. 128 w + 127 per warp)
+__device__ __forceinline__ void kdf_rank(int m, const unsigned short *key, unsigned short *rk,
+                                         unsigned short (*ord)[KD_CTA], unsigned short (*wcnt)[256],
+                                         unsigned *dstart, unsigned *wsum)
+{
+    const int tid = threadIdx.x, lane = lane_id(), w = warp_id();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int i = tid; i < m; i += blockDim.x) ord[0][i] = (unsigned short)i;
+    int cur = 0;
+    for (int sh = 0; sh < 16; sh += 8) {
+        for (int i = tid; i < 8 * 256; i += blockDim.x) wcnt[i >> 8][i & 255] = 0;
+        __syncthreads();
+        unsigned dd[4], rr[4], ee[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int pos = 128 * w + 32 * j + lane;
+            const bool ok = pos < m;
+            const unsigned e = ok ? ord[cur][pos] : 0u;
+            const unsigned d = ok ? ((unsigned)key[e] >> sh) & 255u : 256u;
+            const unsigned peers = __match_any_sync(FULLW, d);
+            const unsigned before = ok ? wcnt[w][d] : 0u;
+            __syncwarp();
+            if (ok && (peers & lt) == 0) wcnt[w][d] = (unsigned short)(before + __popc(peers));
+            __syncwarp();
+            dd[j] = d;
+            rr[j] = before + __popc(peers & lt);
+            ee[j] = e;
+        }
+        __syncthreads();
+        {
+            // thread d: offsets of the warps within digit d, then digit d's start
+            const int d = tid;
+            unsigned tot = 0;
+#pragma unroll
+            for (int ww = 0; ww < 8; ww++) {
+                const unsigned t = wcnt[ww][d];
+                wcnt[ww][d] = (unsigned short)tot;
+                tot += t;
+            }
+            unsigned x = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(FULLW, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) wsum[w] = x;
+            __syncthreads();
+            unsigned pre = 0;
+            for (int ww = 0; ww < w; ww++) pre += wsum[ww];
+            dstart[d] = pre + x - tot;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (dd[j] < 256u) ord[cur ^ 1][dstart[dd[j]] + wcnt[w][dd[j]] + rr[j]] = (unsigned short)ee[j];
+        __syncthreads();
+        cur ^= 1;
+    }
+    for (int i = tid; i < m; i += blockDim.x) rk[ord[cur][i]] = (unsigned short)i;
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(256) k_kd_finish(LevelBufs L, NodeArrays nd, const int4 *ranges, const int *count,
                                                      const float4 *wpos, const float4 *wvel, unsigned *vals)
 {
-    __shared__ unsigned short q[6][KD_CTA];
     __shared__ unsigned slot[KD_CTA];
-    __shared__ unsigned long long key[KD_CTA];
-    __shared__ unsigned short perm[KD_CTA];
+    __shared__ unsigned short rk[KDF_ROUNDS][KD_CTA];
+    __shared__ unsigned short key[KD_CTA];
+    __shared__ unsigned short pm[2][KD_CTA];  // ranking order, then position -> element
+    __shared__ unsigned short wcnt[8][256];
+    __shared__ unsigned dstart[256];
+    __shared__ unsigned wsum[8];
+    __shared__ unsigned bm[KDF_SUB][32];
+    __shared__ unsigned short pre[KDF_SUB][32];
+    const int tid = threadIdx.x, lane = lane_id(), w = warp_id();
     const int nr = *count;
     for (int ri = blockIdx.x; ri < nr; ri += gridDim.x) {
         const int4 rg = ranges[ri];
@@ -1941,59 +2068,68 @@ __global__ void __launch_bounds__(256) k_kd_finish(LevelBufs L, NodeArrays nd, c
         const float ix = nd.sigx[node] > 0 ? (float)(1.0 / nd.sigx[node]) : 0.f;
         const float iv = nd.sigv[node] > 0 ? (float)(1.0 / nd.sigv[node]) : 0.f;
         const float4 pref = L.ref[2 * k], vref = L.ref[2 * k + 1];
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            const unsigned sl = vals[P0 + i];
-            slot[i] = sl;
-            for (int a = 0; a < 6; a++) q[a][i] = (unsigned short)kd_coord(wpos, wvel, sl, a, pref, vref, ix, iv);
-            perm[i] = (unsigned short)i;
-        }
-        int P2 = 1;
-        while (P2 < m) P2 <<= 1;
         const int R = kd_rounds(m, 32);
+        for (int i = tid; i < m; i += blockDim.x) slot[i] = vals[P0 + i];
         __syncthreads();
         for (int r = 0; r < R; r++) {
             const int axis = (d0 + r) % 6;
-            for (int j = threadIdx.x; j < P2; j += blockDim.x) {
-                unsigned long long kk = ~0ull;
-                if (j < m) {
-                    int start = 0, size = m;
-                    for (int i = 0; i < r && size > 32; i++) {
-                        const int h = kd_split(size);
-                        if (j - start < h) {
-                            size = h;
-                        } else {
-                            start += h;
-                            size -= h;
-                        }
-                    }
-                    const unsigned e = perm[j];
-                    const unsigned v = size > 32 ? q[axis][e] : 0u;
-                    kk = ((unsigned long long)(start / 32) << 40) | ((unsigned long long)v << 16) | j;
+            for (int i = tid; i < m; i += blockDim.x)
+                key[i] = (unsigned short)kd_coord(wpos, wvel, slot[i], axis, pref, vref, ix, iv);
+            __syncthreads();
+            kdf_rank(m, key, rk[r], pm, wcnt, dstart, wsum);
+        }
+        int cur = 0;
+        for (int i = tid; i < m; i += blockDim.x) pm[0][i] = (unsigned short)i;
+        for (int r = 0; r < R; r++) {
+            for (int i = tid; i < KDF_SUB * 32; i += blockDim.x) bm[i >> 5][i & 31] = 0u;
+            __syncthreads();
+            for (int j = tid; j < m; j += blockDim.x) {
+                int start = 0, size = m, sub = 0;
+                for (int i = 0; i < r && size > 32; i++) {
+                    const int h = kd_split(size);
+                    const int hi = j - start >= h ? 1 : 0;
+                    start = hi ? start + h : start;
+                    size = hi ? size - h : h;
+                    sub = 2 * sub + hi;
                 }
-                key[j] = kk;
+                if (size > 32) {
+                    const unsigned q = rk[r][pm[cur][j]];
+                    atomicOr(&bm[sub][q >> 5], 1u << (q & 31));
+                }
             }
             __syncthreads();
-            for (int kb = 2; kb <= P2; kb <<= 1)
-                for (int jb = kb >> 1; jb > 0; jb >>= 1) {
-                    for (int t = threadIdx.x; t < P2 / 2; t += blockDim.x) {
-                        const int i = 2 * jb * (t / jb) + (t % jb), l = i + jb;
-                        const bool up = (i & kb) == 0;
-                        const unsigned long long x = key[i], y = key[l];
-                        if ((x > y) == up) {
-                            key[i] = y;
-                            key[l] = x;
-                        }
-                    }
-                    __syncthreads();
+            for (int sb = w; sb < (1 << r); sb += 8) {
+                const unsigned c = __popc(bm[sb][lane]);
+                unsigned x = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned y = __shfl_up_sync(FULLW, x, o);
+                    if (lane >= o) x += y;
                 }
-            // new order: position j holds the element that was at position key & 0xffff
-            unsigned short np[KD_CTA / 256];
-            for (int j = threadIdx.x, c = 0; j < m; j += blockDim.x, c++) np[c] = perm[(int)(key[j] & 0xffffu)];
+                pre[sb][lane] = (unsigned short)(x - c);
+            }
             __syncthreads();
-            for (int j = threadIdx.x, c = 0; j < m; j += blockDim.x, c++) perm[j] = np[c];
+            for (int j = tid; j < m; j += blockDim.x) {
+                int start = 0, size = m, sub = 0;
+                for (int i = 0; i < r && size > 32; i++) {
+                    const int h = kd_split(size);
+                    const int hi = j - start >= h ? 1 : 0;
+                    start = hi ? start + h : start;
+                    size = hi ? size - h : h;
+                    sub = 2 * sub + hi;
+                }
+                const unsigned short e = pm[cur][j];
+                int np = j;
+                if (size > 32) {
+                    const unsigned q = rk[r][e];
+                    np = start + pre[sub][q >> 5] + __popc(bm[sub][q >> 5] & ((1u << (q & 31)) - 1u));
+                }
+                pm[cur ^ 1][np] = e;
+            }
             __syncthreads();
+            cur ^= 1;
         }
-        for (int j = threadIdx.x; j < m; j += blockDim.x) vals[P0 + j] = slot[perm[j]];
+        for (int j = tid; j < m; j += blockDim.x) vals[P0 + j] = slot[pm[cur][j]];
         __syncthreads();
     }
 }
@@ -2484,18 +2620,19 @@ static rs_status launch_nn(rs_ctx *ctx, const char *name, int64_t W, const Level
                            const NodeArrays &nd, const int64_t *bo, const BoxStore &boxes, const MemberStore &ms,
                            const float *R2, const float *STOP, int redo_failed, float *dnn)
 {
+    const int64_t g = ceil_div(W, NN_WARPS);
     switch (ctx->tune.nn_blocks_per_sm) {
     case 5:
-        RS_LAUNCH(ctx, name, k_bvh_nn<5>, ceil_div(W, W_WARPS), W_WARPS * 32, 0, L, JF, nd, bo, boxes, ms, R2, STOP,
-                  redo_failed, dnn, ctx->d_status);
+        RS_LAUNCH(ctx, name, k_bvh_nn<5>, g, NN_WARPS * 32, 0, L, JF, nd, bo, boxes, ms, R2, STOP, redo_failed, dnn,
+                  ctx->d_status);
         break;
     case 7:
-        RS_LAUNCH(ctx, name, k_bvh_nn<7>, ceil_div(W, W_WARPS), W_WARPS * 32, 0, L, JF, nd, bo, boxes, ms, R2, STOP,
-                  redo_failed, dnn, ctx->d_status);
+        RS_LAUNCH(ctx, name, k_bvh_nn<7>, g, NN_WARPS * 32, 0, L, JF, nd, bo, boxes, ms, R2, STOP, redo_failed, dnn,
+                  ctx->d_status);
         break;
     default:
-        RS_LAUNCH(ctx, name, k_bvh_nn<6>, ceil_div(W, W_WARPS), W_WARPS * 32, 0, L, JF, nd, bo, boxes, ms, R2, STOP,
-                  redo_failed, dnn, ctx->d_status);
+        RS_LAUNCH(ctx, name, k_bvh_nn<6>, g, NN_WARPS * 32, 0, L, JF, nd, bo, boxes, ms, R2, STOP, redo_failed, dnn,
+                  ctx->d_status);
     }
     return RS_OK;
 }
@@ -2661,28 +2798,39 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
             int64_t maxn = 0;
             RS_TRY(rs_read_i64(ctx, tot + 3, 1, &maxn, "rs_refine6d"));
             RS_WS(ctx, int64_t, kw, WS_RF_MISC5, 2 * (K + 1) + 8);
-            int64_t *kseg = kw, *ktot = kw + (K + 1);
-            RS_LAUNCH(ctx, "rf_kd_blocks", k_kd_blocks, ceil_div(K, 256), 256, 0, (const int *)cur, (int)K, nd, kseg);
-            RS_CUDA(ctx, cudaMemsetAsync(kseg + K, 0, sizeof(int64_t), ctx->stream));
-            RS_TRY(rs_scan_i64(ctx, kseg, K + 1, ktot));
-            int64_t NS;
-            RS_TRY(rs_read_i64(ctx, ktot, 1, &NS, "rs_refine6d"));
-            int sbits = 0;
-            while (sbits < 40 && (NS >> sbits) != 0) sbits++;
-            // 32-bit keys (half the bytes, four passes) while the blocks fit in 16 bits
-            const int key32 = 16 + sbits <= 32 ? 1 : 0;
+            int64_t *kseg = kw, *aoff = kw + (K + 1), *ktot = kw + 2 * (K + 1);
+            RS_WS(ctx, unsigned, vcur, WS_RF_KDV, LM);
+            RS_LAUNCH(ctx, "rf_kd_init", k_kd_init, T, TQ, 0, L, nd, vcur);
+            // each round sorts only the members of the nodes still being
+            // split, so a node costs the rounds its own size needs, not the
+            // largest node's; the range keys shrink with the active blocks
             const int R = kd_rounds(maxn, KD_CTA);
-            const unsigned *vsorted = nullptr;
             for (int r = 0; r < R; r++) {
-                RS_LAUNCH(ctx, "rf_kd_keys", k_kd_keys, T, TQ, 0, L, nd, (const int64_t *)kseg, (const float4 *)wpos,
-                          (const float4 *)wvel, vsorted, (unsigned long long *)k0, v0, r, key32);
+                RS_LAUNCH(ctx, "rf_kd_active", k_kd_active, ceil_div(K, 256), 256, 0, (const int *)cur, (int)K, nd,
+                          r, kseg, aoff);
+                RS_CUDA(ctx, cudaMemsetAsync(kseg + K, 0, sizeof(int64_t), ctx->stream));
+                RS_CUDA(ctx, cudaMemsetAsync(aoff + K, 0, sizeof(int64_t), ctx->stream));
+                RS_TRY(rs_scan_i64(ctx, kseg, K + 1, ktot));
+                RS_TRY(rs_scan_i64(ctx, aoff, K + 1, ktot + 1));
+                int64_t tots[2];
+                RS_TRY(rs_read_i64(ctx, ktot, 2, tots, "rs_refine6d"));
+                const int64_t NS = tots[0], NA = tots[1];
+                if (NA <= 0) break;
+                int sbits = 0;
+                while (sbits < 40 && (NS >> sbits) != 0) sbits++;
+                // 32-bit keys (half the bytes, fewer passes) while the blocks fit in 16 bits
+                const int key32 = 16 + sbits <= 32 ? 1 : 0;
+                RS_LAUNCH(ctx, "rf_kd_keys", k_kd_keys, T, TQ, 0, L, nd, (const int64_t *)kseg, (const int64_t *)aoff,
+                          (const float4 *)wpos, (const float4 *)wvel, (const unsigned *)vcur,
+                          (unsigned long long *)k0, v0, r, key32);
                 bool kalt = false;
                 if (key32)
-                    RS_TRY(rs_radix_sort_u32(ctx, (uint32_t *)k0, (uint32_t *)k1, v0, v1, LM, 16 + sbits, &kalt,
+                    RS_TRY(rs_radix_sort_u32(ctx, (uint32_t *)k0, (uint32_t *)k1, v0, v1, NA, 16 + sbits, &kalt,
                                              "sort_kd"));
                 else
-                    RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, LM, 16 + sbits, &kalt, "sort_kd"));
-                vsorted = kalt ? v1 : v0;
+                    RS_TRY(rs_radix_sort_u64(ctx, k0, k1, v0, v1, NA, 16 + sbits, &kalt, "sort_kd"));
+                RS_LAUNCH(ctx, "rf_kd_back", k_kd_back, T, TQ, 0, L, nd, (const int64_t *)aoff,
+                          (const unsigned *)(kalt ? v1 : v0), vcur);
             }
             // ranges of at most KD_CTA members finish in one CTA each
             const int64_t rcap = ceil_div(LM, 32) + K;
@@ -2691,16 +2839,11 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
             RS_CUDA(ctx, cudaMemsetAsync(kcount, 0, sizeof(int), ctx->stream));
             RS_LAUNCH(ctx, "rf_kd_ranges", k_kd_ranges, ceil_div(K, 128), 128, 0, L, nd, kranges, kcount, (int)rcap,
                       ctx->d_status);
-            if (R == 0)  // every member in its own position: round 0 writes the slots
-                RS_LAUNCH(ctx, "rf_kd_keys", k_kd_keys, T, TQ, 0, L, nd, (const int64_t *)kseg,
-                          (const float4 *)wpos, (const float4 *)wvel, vsorted, (unsigned long long *)k0, v0, 0,
-                          key32);
-            unsigned *vfin = R > 0 ? (unsigned *)vsorted : v0;
             RS_LAUNCH(ctx, "rf_kd_finish", k_kd_finish, (int64_t)ctx->num_sms * 8, 256, 0, L, nd,
-                      (const int4 *)kranges, (const int *)kcount, (const float4 *)wpos, (const float4 *)wvel, vfin);
-            vsorted = vfin;
+                      (const int4 *)kranges, (const int *)kcount, (const float4 *)wpos, (const float4 *)wvel, vcur);
+            const unsigned *vsorted = vcur;
             {
-                unsigned *kdest = (unsigned *)(vsorted == v0 ? v1 : v0);
+                unsigned *kdest = v0;
                 RS_LAUNCH(ctx, "rf_kd_place", k_kd_place, T, TQ, 0, L, nd, vsorted, (const float4 *)wpos,
                           (const float4 *)wvel, (const int *)widx, wpos2, wvel2, widx2, kdest);
                 RS_LAUNCH(ctx, "rf_lvl_copyback", k_lvl_copyback, ceil_div(LM, 256), 256, 0, LM,
@@ -2835,18 +2978,21 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         RS_LAUNCH(ctx, "rf_lvl_iota", k_lvl_iota, T, TQ, 0, L, nd, uf, csize, cmin);
         RS_LAUNCH(ctx, "rf_bvh_linkbox", k_bvh_linkbox, K, 256, 0, L, nd, (const int64_t *)bo, boxes,
                   (const float4 *)wpos, (const float4 *)wvel, (const float *)dnn, uf, ctx->d_status);
-        switch (ctx->tune.link_blocks_per_sm) {
-        case 4:
-            RS_LAUNCH(ctx, "rf_lvl_link", k_bvh_link<4>, T, TQ, 0, L, nd, (const int64_t *)bo, boxes, ms,
-                      (const float *)dnn, uf, ctx->d_status);
-            break;
-        case 6:
-            RS_LAUNCH(ctx, "rf_lvl_link", k_bvh_link<6>, T, TQ, 0, L, nd, (const int64_t *)bo, boxes, ms,
-                      (const float *)dnn, uf, ctx->d_status);
-            break;
-        default:
-            RS_LAUNCH(ctx, "rf_lvl_link", k_bvh_link<5>, T, TQ, 0, L, nd, (const int64_t *)bo, boxes, ms,
-                      (const float *)dnn, uf, ctx->d_status);
+        {
+            const int64_t njobs = T * (TQ / 32), lg = ceil_div(njobs, LK_WARPS);
+            switch (ctx->tune.link_blocks_per_sm) {
+            case 4:
+                RS_LAUNCH(ctx, "rf_lvl_link", k_bvh_link<4>, lg, LK_WARPS * 32, 0, L, nd, (const int64_t *)bo, boxes,
+                          ms, (const float *)dnn, uf, ctx->d_status);
+                break;
+            case 6:
+                RS_LAUNCH(ctx, "rf_lvl_link", k_bvh_link<6>, lg, LK_WARPS * 32, 0, L, nd, (const int64_t *)bo, boxes,
+                          ms, (const float *)dnn, uf, ctx->d_status);
+                break;
+            default:
+                RS_LAUNCH(ctx, "rf_lvl_link", k_bvh_link<5>, lg, LK_WARPS * 32, 0, L, nd, (const int64_t *)bo, boxes,
+                          ms, (const float *)dnn, uf, ctx->d_status);
+            }
         }
         RS_LAUNCH(ctx, "rf_lvl_comp", k_lvl_comp, T, TQ, 0, L, nd, (const int *)widx, uf, csize, cmin,
                   ctx->d_status);
@@ -2986,6 +3132,7 @@ extern "C" rs_status rs_refine6d_sampled(rs_ctx *ctx, const float *pos, const fl
         return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_refine6d: subset size must be 0 or in [1024, 2^31)");
     if (n >= ((int64_t)1 << 31)) return rs_fail(ctx, RS_ERR_TOO_LARGE, "rs_refine6d: n >= 2^31");
     if ((double)(float)box != box) return rs_fail(ctx, RS_ERR_INVALID_ARG, "rs_refine6d: box must be a float32 value");
+    RsRange range("rs_refine6d");
     int64_t cap = 0;
     {
         int64_t h[2];
