@@ -92,9 +92,11 @@ const char *rs_last_error(const rs_ctx *ctx);
  * which order).  A context starts with rs_tuning_default's values, which
  * are the ones the library's tuner chose on a GB300 (the tuner, its
  * coordinate descent and its result check are in the Python package).
- *   link_blocks_per_sm  big-node link search: resident 256-thread blocks per
- *                       SM the kernel is compiled for (4, 5 or 6);
- *   nn_blocks_per_sm    big-node nearest-neighbour search (5, 6 or 7);
+ *   link_blocks_per_sm  big-node link search: resident warps per SM the
+ *                       kernel is compiled for, in units of eight (4, 5 or 6:
+ *                       32, 40 or 48 warps);
+ *   nn_blocks_per_sm    big-node nearest-neighbour search, the same (5, 6
+ *                       or 7);
  *   kd_levels           big-node levels whose members are put in k-d order
  *                       (0-3; deeper levels keep their parent's order);
  *   bracket_min         big nodes above this many members search with the

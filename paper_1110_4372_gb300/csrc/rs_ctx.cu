@@ -88,7 +88,7 @@ extern "C" void rs_tuning_default(rs_tuning *t)
     if (!t) return;
     t->link_blocks_per_sm = 5;
     t->nn_blocks_per_sm = 6;
-    t->kd_levels = 2;
+    t->kd_levels = 3;
     t->bracket_min = 4096;
     t->mid_max = 256;
     t->tiny_max = 32;
