@@ -57,8 +57,8 @@ BYTES_ASSIGN_PER_MEMBER = 28
 # scaled to a step by the units processed.  An entry is dropped when its
 # kernel changes.
 NCU_TRAFFIC_PER_UNIT = {
-    "rf_lvl_link": 321969408 / 8612074,
-    "rf_lvl_nn": 241535488 / 8612074,
+    "rf_lvl_link": 325757952 / 8612074,
+    "rf_lvl_nn": 241497088 / 8612074,
 }
 
 # Which units each kernel processes per step (for its algorithmic bytes).

@@ -51,38 +51,56 @@ def timed_call(rsgpu, ctx, pos, vel, box, halo, labels, reps):
     return statistics.median(times)
 
 
-def tune(rsgpu, ctx, pos, vel, box, reps=3, sweeps=2, log=print):
-    """Coordinate descent from the library's defaults.  Returns (best table,
-    its ms, default ms, trials)."""
-    import torch
-    n = pos.shape[0]
-    halo = torch.empty(n, dtype=torch.int32, device=pos.device)
-    labels = torch.empty(n, dtype=torch.int32, device=pos.device)
-    base = rsgpu.rs_tuning_default()
-    rsgpu.rs_set_tuning(ctx, **base)
-    base_ms = timed_call(rsgpu, ctx, pos, vel, box, halo, labels, reps)
-    ref_halo, ref_lab = halo.clone(), labels.clone()
+def descend(base, space, measure, sweeps=2, log=print, margin=0.995):
+    """Coordinate descent from the table `base` over `space` (choice -> its
+    candidate values).  measure(table) returns (ms, same_result); a candidate
+    becomes the best only when its time is below margin x the best so far, and
+    a candidate whose result differs stops the descent.  A sweep that keeps no
+    candidate ends it.  Returns (best table, its ms, base ms, trials)."""
+    base_ms, same = measure(dict(base))
+    if not same:
+        raise RuntimeError("the starting table's result differs from the reference")
     best, best_ms = dict(base), base_ms
     trials = [{"tuning": dict(base), "ms": base_ms}]
     log(f"defaults: {base_ms:.2f} ms")
     for sweep in range(sweeps):
         improved = False
-        for key, values in SPACE.items():
+        for key, values in space.items():
             for v in values:
                 if v == best[key]:
                     continue
                 cand = dict(best, **{key: v})
-                rsgpu.rs_set_tuning(ctx, **cand)
-                ms = timed_call(rsgpu, ctx, pos, vel, box, halo, labels, reps)
-                same = bool(torch.equal(halo, ref_halo) and torch.equal(labels, ref_lab))
+                ms, same = measure(cand)
                 trials.append({"tuning": cand, "ms": ms, "same_result": same})
                 if not same:
                     raise RuntimeError(f"launch choice {key}={v} changed the result")
                 log(f"sweep {sweep} {key}={v}: {ms:.2f} ms (best {best_ms:.2f})")
-                if ms < best_ms * 0.995:
+                if ms < best_ms * margin:
                     best, best_ms, improved = cand, ms, True
         if not improved:
             break
+    return best, best_ms, base_ms, trials
+
+
+def tune(rsgpu, ctx, pos, vel, box, reps=3, sweeps=2, log=print):
+    """Coordinate descent from the library's defaults on the resident
+    workload; every candidate's 3D labels and halo ids must equal those of
+    the defaults.  Returns (best table, its ms, default ms, trials)."""
+    import torch
+    n = pos.shape[0]
+    halo = torch.empty(n, dtype=torch.int32, device=pos.device)
+    labels = torch.empty(n, dtype=torch.int32, device=pos.device)
+    ref = {}
+
+    def measure(table):
+        rsgpu.rs_set_tuning(ctx, **table)
+        ms = timed_call(rsgpu, ctx, pos, vel, box, halo, labels, reps)
+        if not ref:
+            ref["halo"], ref["labels"] = halo.clone(), labels.clone()
+            return ms, True
+        return ms, bool(torch.equal(halo, ref["halo"]) and torch.equal(labels, ref["labels"]))
+
+    best, best_ms, base_ms, trials = descend(rsgpu.rs_tuning_default(), SPACE, measure, sweeps, log)
     rsgpu.rs_set_tuning(ctx, **best)
     return best, best_ms, base_ms, trials
 

@@ -85,3 +85,29 @@ def test_shipped_tuning_record_equals_the_library_defaults():
     assert rec["tuned"] == rsgpu.rs_tuning_default()
     assert all(t.get("same_result", True) for t in rec["trials"])
     assert rec["tuned_ms"] <= min(t["ms"] for t in rec["trials"]) * 1.005
+
+
+def test_tuner_descent():
+    """The tuner's coordinate descent: keeps a candidate only when it beats
+    the best by the margin, measures no table twice in a sweep, ends after a
+    sweep that keeps nothing, and stops when a candidate changes the result."""
+    import pytest
+    from paper_1110_4372_gb300 import tune
+    space = {"a": [1, 2, 3], "b": [10, 20], "c": [0, 1]}
+    cost = {("a", 1): 0.0, ("a", 2): -5.0, ("a", 3): -4.0, ("b", 10): 0.0, ("b", 20): -0.2,
+            ("c", 0): 0.0, ("c", 1): -2.0}
+    seen = []
+
+    def measure(t):
+        seen.append(dict(t))
+        return 100.0 + sum(cost[(k, v)] for k, v in t.items()), True
+
+    best, best_ms, base_ms, trials = tune.descend({"a": 1, "b": 10, "c": 0}, space, measure, sweeps=3,
+                                                  log=lambda m: None)
+    # b=20 saves 0.2 ms of ~95: inside the 0.5% margin, so not kept
+    assert best == {"a": 2, "b": 10, "c": 1} and best_ms == 93.0 and base_ms == 100.0
+    assert len(trials) == len(seen)
+    # sweep 0 moves a and c, sweep 1 keeps nothing and ends the descent
+    assert len(seen) == 1 + 4 + 4
+    with pytest.raises(RuntimeError, match="changed the result"):
+        tune.descend({"a": 1, "b": 10, "c": 0}, space, lambda t: (100.0, t["b"] != 20), log=lambda m: None)
