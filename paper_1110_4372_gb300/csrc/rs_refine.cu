@@ -2614,8 +2614,8 @@ size_t tree_bytes(int64_t M, int64_t cap)
 
 }  // namespace
 
-// the big-node nearest-neighbour search, compiled for 5, 6 or 7 resident
-// blocks per SM (rs_tuning::nn_blocks_per_sm)
+// the big-node nearest-neighbour search, compiled for 40, 48 or 56 resident
+// warps per SM (rs_tuning::nn_blocks_per_sm = 5, 6 or 7, in units of eight)
 static rs_status launch_nn(rs_ctx *ctx, const char *name, int64_t W, const LevelBufs &L, const WarpJobs &JF,
                            const NodeArrays &nd, const int64_t *bo, const BoxStore &boxes, const MemberStore &ms,
                            const float *R2, const float *STOP, int redo_failed, float *dnn)
@@ -2979,6 +2979,8 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         RS_LAUNCH(ctx, "rf_bvh_linkbox", k_bvh_linkbox, K, 256, 0, L, nd, (const int64_t *)bo, boxes,
                   (const float4 *)wpos, (const float4 *)wvel, (const float *)dnn, uf, ctx->d_status);
         {
+            // one warp per leaf job, LK_WARPS to a block; compiled for 8 x
+            // rs_tuning::link_blocks_per_sm resident warps per SM
             const int64_t njobs = T * (TQ / 32), lg = ceil_div(njobs, LK_WARPS);
             switch (ctx->tune.link_blocks_per_sm) {
             case 4:
