@@ -370,7 +370,11 @@ typedef struct {
  * positions go first, the velocities travel on a second stream of the
  * context while the 3D FOF and the group sort run, and fof_labels comes back
  * on it while the refinement runs; the caller's buffers must stay valid
- * until the call returns.  fof_labels and stats may be NULL.  Synchronises. */
+ * until the call returns.  Positions, velocities and halo ids in mapped
+ * pinned memory with 16-byte aligned addresses are moved by a copy kernel
+ * that reads or writes the host buffer in place (other host memory goes
+ * through cudaMemcpyAsync).  fof_labels and stats may be NULL.
+ * Synchronises. */
 rs_status rs_find_halos(rs_ctx *ctx, const float *pos, const float *vel, int32_t stride, int64_t n, double box,
                         const rs_params *params, int32_t *fof_labels, int32_t *halo_id, rs_stats *stats,
                         int32_t host_buffers);
