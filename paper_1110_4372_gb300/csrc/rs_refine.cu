@@ -1803,7 +1803,7 @@ __global__ void k_bracket_check(LevelBufs L, float *R2, const float *STOP, int *
     }
 }
 
-// ---- level-0 ordering: k-d splits at leaf-aligned medians ----
+// ---- big-node member order: k-d splits at leaf-aligned medians ----
 // A node's member range is split recursively: a range of m > 32 members
 // splits at h = m/2 rounded up to a multiple of 32, the h members with the
 // smallest coordinate on the round's axis going left, the axes cycling
@@ -2792,9 +2792,9 @@ static rs_status refine_impl(rs_ctx *ctx, const float *pos, const float *vel, in
         while (rbits < 32 && ((uint64_t)(K - 1) >> rbits) != 0) rbits++;
         if (level < ctx->tune.kd_levels) {
             // order each big node's members by k-d splits at leaf-aligned
-            // medians (levels 0 and 1 by default, where most of the search
-            // work is); deeper levels keep this order through the stable
-            // child partition below
+            // medians (levels 0-2 by default, where most of the search work
+            // is); deeper levels keep this order through the stable child
+            // partition below
             int64_t maxn = 0;
             RS_TRY(rs_read_i64(ctx, tot + 3, 1, &maxn, "rs_refine6d"));
             RS_WS(ctx, int64_t, kw, WS_RF_MISC5, 2 * (K + 1) + 8);
