@@ -69,3 +69,42 @@ def test_group_sizes_without_drawing_particles():
     assert np.array_equal(synth.group_sizes("c4s", first=17, count=9), np.diff(g.offsets))
     s = synth.group_sizes("c4", first=0, count=2000)
     assert s.min() >= 20 and s.max() <= 500_000
+
+
+def test_recipe_mass_function_nfw_profile_and_velocities():
+    """The catalogue recipe: host counts follow dN/dn ∝ n^-1.9 (the
+    discretised inverse CDF), a host's particles follow the NFW enclosed
+    mass of a concentration in [5, 15] inside its virial radius, and halo
+    and background velocities have the stated dispersions."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    nmin, nmax = 20, 200_000
+    n = synth._power_law_counts(rng, 200_000, nmin, nmax)
+    a = 1.0 - 1.9
+    for m in (20, 25, 40, 100, 1000, 20_000):
+        cdf = (nmin ** a - (m + 1.0) ** a) / (nmin ** a - (nmax + 1.0) ** a)
+        assert abs(np.mean(n <= m) - cdf) < 0.005, m
+
+    c = synth.generate("c2")
+    hosts = np.flatnonzero(c.comp_parent < 0)
+    orig = c.comp_n.astype(np.float64).copy()
+    np.add.at(orig, c.comp_parent[c.comp_parent >= 0], c.comp_n[c.comp_parent >= 0])
+    nbar = c.n / c.box ** 3
+    m_nfw = lambda x: np.log1p(x) - x / (1.0 + x)  # noqa: E731
+    checked = 0
+    for h in hosts[np.argsort(c.comp_n[hosts])[::-1][:5]]:
+        sel = c.truth == h
+        d = c.pos[sel].astype(np.float64) - c.comp_center[h]
+        d -= c.box * np.round(d / c.box)
+        q = np.linalg.norm(d, axis=1) / (3.0 * orig[h] / (4.0 * np.pi * 360.0 * nbar)) ** (1.0 / 3.0)
+        assert q.max() <= 1.0 + 1e-4
+        for r in (0.1, 0.3, 0.6):
+            emp = np.mean(q <= r)
+            lo, hi = m_nfw(5 * r) / m_nfw(5.0), m_nfw(15 * r) / m_nfw(15.0)
+            tol = 4.0 / np.sqrt(sel.sum())
+            assert lo - tol <= emp <= hi + tol, (h, r, emp, lo, hi)
+        sig = np.std(c.vel[sel].astype(np.float64), axis=0)
+        assert np.all(np.abs(sig / (300.0 * (orig[h] / 4000.0) ** (1.0 / 3.0)) - 1.0) < 6.0 / np.sqrt(sel.sum()) + 0.01)
+        checked += 1
+    assert checked == 5
+    bg = c.truth < 0
+    assert abs(np.std(c.vel[bg].astype(np.float64)) / 20.0 - 1.0) < 0.01
