@@ -153,3 +153,28 @@ def test_empty_and_single():
     assert lab.shape == (0,) and tie == 0
     lab, _, _ = oracle.fof3d(np.array([[1, 2, 3]], np.float32), 10.0, l=0.1)
     assert lab.tolist() == [0]
+
+
+def test_random_small_boxes_vs_brute():
+    """Property check: random tiny catalogues (clumps and a background, any
+    box side and linking length the grid accepts) give the brute-force
+    partition."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=60, deadline=None, derandomize=True)
+    @hyp.given(seed=st.integers(0, 2 ** 32 - 1), n=st.integers(1, 300), box=st.floats(1.0, 50.0),
+               rel=st.floats(0.02, 0.3), clumps=st.integers(0, 4))
+    def check(seed, n, box, rel, clumps):
+        rng = np.random.default_rng(seed)
+        p = rng.random((n, 3)) * box
+        for c in range(clumps):
+            k = rng.integers(0, n + 1)
+            p[:k] = rng.random(3) * box + rng.normal(0.0, rel * box * 0.2, (k, 3))
+        p = synth.wrap(p, box)
+        box32 = float(np.float32(box))
+        l = rel * box32
+        lab, _, _ = oracle.fof3d(p, box32, l=l)
+        assert np.array_equal(lab, brute_labels(p, box32, l))
+
+    check()
